@@ -1,0 +1,171 @@
+/*
+ * aqc.h -- C ABI of the GB300 adiabatic-evolution hot path (libaqc.so).
+ *
+ * The library integrates the time-dependent Schroedinger equation i d/dt psi = H(t) psi
+ * (hbar = 1; Eq. schroedinger of arXiv:1311.3938) for a 2^n-amplitude state, where
+ *     H(t) = A(s) H_A + B(s) H_B + C(s) H_C                     (Eq. aqc, Eq. nlpath)
+ * and each group H_g is stored in the paper's Sparse Quantum Hamiltonian form
+ * (Sec. I.A, Eq. SQH-Hamiltonian): a list of Pauli products with real prefactors, plus
+ * Exact-Cover-3 clause penalties (Eq. hci, Eq. sat).  The integrator is a fourth-order
+ * predictor-corrector with one H|psi> per step (Sec. I.B): Adams-Bashforth-4 predictor,
+ * Adams-Moulton-4 corrector in PEC mode, fixed step h = T/N, started by three classical
+ * Runge-Kutta-4 steps.  All arithmetic runs in CUDA kernels for sm_103a.
+ *
+ * Conventions (all entry points)
+ *   - Return value: AQC_OK (0) or a negative AQC_E_* code; the context keeps a message
+ *     readable with aqc_last_error().  Errors leave the context usable unless stated.
+ *   - Basis index z: bit (q-1) of z is qubit q (Eq. ztensor and the formula after it).
+ *   - State vectors: interleaved complex, (re, im) per amplitude, 2^n amplitudes; complex128
+ *     (16 bytes/amplitude) for AQC_C128 or complex64 (8 bytes/amplitude) for AQC_C64.
+ *   - Host arrays passed in are copied; the caller keeps ownership.
+ *   - Device memory: the library allocates none.  The caller passes one device workspace
+ *     of at least aqc_workspace_bytes() bytes at aqc_create(); it must stay valid until
+ *     aqc_destroy().  All vectors, tables and reduction slots live in it.
+ *   - Stream: all device work of a context is ordered on the stream given at creation (or
+ *     aqc_set_stream()).  Functions that return host values synchronise that stream; the
+ *     others only enqueue work.
+ *   - Sizes: 1 <= n <= 31; masks must be < 2^n; clause bits distinct and < n.
+ */
+#ifndef AQC_H
+#define AQC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- codes ------------------------------------------------------------------------- */
+#define AQC_OK 0
+#define AQC_E_INVAL (-1)        /* bad argument (size, mask, pointer, enum)              */
+#define AQC_E_NOMEM (-2)        /* workspace too small / host allocation failed           */
+#define AQC_E_CUDA (-3)         /* a CUDA runtime call failed (message has the CUDA text) */
+#define AQC_E_NUMERIC (-4)      /* non-finite value detected in a reduction               */
+#define AQC_E_STATE (-5)        /* call out of order (e.g. propagate before a schedule)   */
+#define AQC_E_UNSUPPORTED (-6)  /* a term no layout can hold, or a size beyond the limits */
+
+#define AQC_C128 0 /* complex128 state, FP64 arithmetic                                   */
+#define AQC_C64 1  /* complex64 state, FP32 arithmetic, FP64 reductions                   */
+
+#define AQC_GRP_A 0 /* weight A(s), e.g. the initial Hamiltonian H_i                     */
+#define AQC_GRP_B 1 /* weight B(s), e.g. the final Hamiltonian H_f                       */
+#define AQC_GRP_C 2 /* weight C(s), e.g. a third path Hamiltonian                        */
+
+#define AQC_PEN_INDICATOR 0 /* penalty [k != 1], k = number of 1-bits of the clause      */
+#define AQC_PEN_SQUARED 1   /* penalty (1 - k)^2 (Eq. hci)                               */
+
+#define AQC_S_LINEAR 0     /* s = t/T (Eq. aqc)                                          */
+#define AQC_S_SMOOTHSTEP 1 /* s = 3 tau^2 - 2 tau^3, tau = t/T                           */
+
+#define AQC_INIT_UNIFORM 0     /* |S> = 2^{-n/2} sum_z |z> (Sec. II.A.1)                  */
+#define AQC_INIT_BASIS 1       /* |basis>                                                 */
+#define AQC_INIT_USER_HOST 2   /* copy of a host vector (state precision, interleaved)   */
+#define AQC_INIT_USER_DEVICE 3 /* copy of a device vector (state precision, interleaved) */
+
+typedef struct aqc_ctx aqc_ctx;
+
+typedef struct {
+  int64_t steps_done;  /* grid steps completed since the initial state was set          */
+  int64_t n_steps;     /* N of the grid h = T/N                                          */
+  int64_t evaluations; /* H|psi> evaluations so far                                      */
+  double t;            /* current time (steps_done * h)                                  */
+  double h;            /* step size                                                      */
+  double norm2;        /* ||psi||^2 after the call (FP64 reduction)                      */
+  double max_err_est;  /* max over PEC steps of (19/270) ||y_{n+1} - p_{n+1}||           */
+  double last_err_est; /* the same for the last PEC step                                 */
+  double elapsed_ms;   /* device time of the call (CUDA events on the context stream)    */
+} aqc_stats;
+
+/* ---- lifetime ---------------------------------------------------------------------- */
+
+/* Bytes of device workspace a context for (n_qubits, precision) needs: eight state-sized
+ * vectors (y, p, q, four derivative slots f, one Runge-Kutta accumulator) plus tables and
+ * reduction slots.  Returns 0 for unsupported arguments. */
+size_t aqc_workspace_bytes(int n_qubits, int precision);
+
+/* Create a context on `device` for n_qubits with state precision AQC_C128 or AQC_C64.
+ * `workspace` is a caller-owned device pointer (256-byte aligned) of at least
+ * aqc_workspace_bytes() bytes; `cuda_stream` is a cudaStream_t (NULL = legacy default).
+ * On success *out receives the context. */
+int aqc_create(aqc_ctx **out, int device, int precision, int n_qubits, void *workspace, size_t workspace_bytes,
+               void *cuda_stream);
+
+/* Release the host-side context (the workspace stays the caller's). NULL is ignored. */
+void aqc_destroy(aqc_ctx *ctx);
+
+/* Order all later work of the context on `cuda_stream`. */
+int aqc_set_stream(aqc_ctx *ctx, void *cuda_stream);
+
+/* ---- Hamiltonian (Sec. I.A, Eq. SQH-Hamiltonian) ------------------------------------ */
+
+/* Append n_terms Pauli products to group `group`: term k is
+ *     coef[k] * prod_q P_q,  P_q = X if only xmask bit q set, Z if only zmask bit q set,
+ *                                  Y if both set, identity otherwise,
+ * so Y = i X Z per qubit.  xmask = zmask = 0 is the identity (energy shift m^(0)). */
+int aqc_load_terms(aqc_ctx *ctx, int group, size_t n_terms, const uint64_t *xmask, const uint64_t *zmask,
+                   const double *coef);
+
+/* Append m Exact-Cover-3 clauses (Eq. 1clause) to group `group`: bits[3k..3k+2] are the
+ * 0-based bits of clause k (distinct, < n); its diagonal energy on |z> is
+ * scale * pen(#ones), pen per `penalty` (AQC_PEN_*; Eq. hci for AQC_PEN_SQUARED). */
+int aqc_load_clauses(aqc_ctx *ctx, int group, size_t m, const int32_t *bits, int penalty, double scale);
+
+/* Remove all terms and clauses of all groups. */
+int aqc_clear_hamiltonian(aqc_ctx *ctx);
+
+/* ---- path schedule (Eq. aqc, Eq. nlpath) --------------------------------------------- */
+
+/* Runtime T > 0 and weights A, B, C as cubics in s: w_g(s) = sum_k coef_g[k] s^k, with
+ * s(t) per s_kind (AQC_S_*).  Straight line: A = {1,-1,0,0}, B = {0,1,0,0}, C = 0. */
+int aqc_set_schedule(aqc_ctx *ctx, int s_kind, double T, const double coefA[4], const double coefB[4],
+                     const double coefC[4]);
+
+/* ---- integrator (Sec. I.B) ----------------------------------------------------------- */
+
+/* Fixed-step grid h = T/N.  n_steps > 0 sets N; n_steps == 0 applies the step rule
+ * N = max(4, ceil(T * Lambda / kappa)), Lambda = max over s in [0,1] (1025-point grid) of
+ * sum_g |w_g(s)| * ||H_g||_1 (sum of |prefactors| + max clause penalties), with kappa > 0
+ * (0 selects 0.1; the PEC scheme is stable on the imaginary axis up to about 0.22). */
+int aqc_set_integrator(aqc_ctx *ctx, int64_t n_steps, double kappa);
+
+/* Set psi(0) and reset the integrator to t = 0.  kind = AQC_INIT_*; `basis` for
+ * AQC_INIT_BASIS; `user` points to 2^n interleaved amplitudes in the state precision. */
+int aqc_set_initial_state(aqc_ctx *ctx, int kind, uint64_t basis, const void *user);
+
+/* Advance by up to max_steps grid steps (max_steps < 0: to t = T).  The first three steps
+ * are RK4, the rest PEC.  Fills *stats if non-NULL (then synchronises the stream). */
+int aqc_propagate(aqc_ctx *ctx, int64_t max_steps, aqc_stats *stats);
+
+/* ---- results (Sec. II.B) ------------------------------------------------------------- */
+
+/* Copy psi to dst (2^n interleaved amplitudes in the state precision); dst is device
+ * memory if dst_on_device, else host memory (pinned memory recommended). */
+int aqc_get_state(aqc_ctx *ctx, void *dst, int dst_on_device);
+
+/* |<w|psi>|^2, the success probability P_1 of the solution w (Sec. II.B). */
+int aqc_fidelity(aqc_ctx *ctx, uint64_t w, double *out);
+
+/* <psi|H_group|psi> with unit weight on that group (the final energy E(T) of Sec. II.B
+ * for the group holding H_f).  Not divided by ||psi||^2. */
+int aqc_energy(aqc_ctx *ctx, int group, double *out);
+
+/* ||psi||^2 (FP64 accumulation). */
+int aqc_norm2(aqc_ctx *ctx, double *out);
+
+/* out = H(t) psi for caller-owned device vectors psi, out (state precision, 2^n amplitudes,
+ * distinct, not inside the workspace).  Uses the workspace vector q as scratch, so it
+ * must not overlap a propagation of the same context (same stream ordering suffices).
+ * This is the stand-alone SQH matvec of Sec. I.A. */
+int aqc_hpsi(aqc_ctx *ctx, double t, const void *psi, void *out);
+
+/* Message of the last error of ctx (or of the last failed aqc_create if ctx is NULL). */
+const char *aqc_last_error(const aqc_ctx *ctx);
+
+/* Library version string. */
+const char *aqc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AQC_H */

@@ -1,0 +1,192 @@
+"""ctypes binding of libaqc.so: the C ABI of include/aqc.h under the same names.
+
+Argument marshalling only; every step of the computation runs in the library's CUDA
+kernels.  Loading fails loudly if the library has not been built (no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libaqc.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "aqc.h")
+
+AQC_OK = 0
+AQC_E_INVAL = -1
+AQC_E_NOMEM = -2
+AQC_E_CUDA = -3
+AQC_E_NUMERIC = -4
+AQC_E_STATE = -5
+AQC_E_UNSUPPORTED = -6
+
+AQC_C128 = 0
+AQC_C64 = 1
+AQC_GRP_A, AQC_GRP_B, AQC_GRP_C = 0, 1, 2
+AQC_PEN_INDICATOR, AQC_PEN_SQUARED = 0, 1
+AQC_S_LINEAR, AQC_S_SMOOTHSTEP = 0, 1
+AQC_INIT_UNIFORM, AQC_INIT_BASIS, AQC_INIT_USER_HOST, AQC_INIT_USER_DEVICE = 0, 1, 2, 3
+
+
+class AqcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"aqc error {code}: {msg}")
+        self.code = code
+
+
+class aqc_stats(C.Structure):
+    _fields_ = [
+        ("steps_done", C.c_int64),
+        ("n_steps", C.c_int64),
+        ("evaluations", C.c_int64),
+        ("t", C.c_double),
+        ("h", C.c_double),
+        ("norm2", C.c_double),
+        ("max_err_est", C.c_double),
+        ("last_err_est", C.c_double),
+        ("elapsed_ms", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libaqc.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libaqc.so is not built ({LIB_PATH}); run paper_1311_3938_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, u64, dbl, sz = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double, C.c_size_t
+        sig = {
+            "aqc_workspace_bytes": (sz, [i32, i32]),
+            "aqc_create": (i32, [C.POINTER(vp), i32, i32, i32, vp, sz, vp]),
+            "aqc_destroy": (None, [vp]),
+            "aqc_set_stream": (i32, [vp, vp]),
+            "aqc_load_terms": (i32, [vp, i32, sz, vp, vp, vp]),
+            "aqc_load_clauses": (i32, [vp, i32, sz, vp, i32, dbl]),
+            "aqc_clear_hamiltonian": (i32, [vp]),
+            "aqc_set_schedule": (i32, [vp, i32, dbl, vp, vp, vp]),
+            "aqc_set_integrator": (i32, [vp, i64, dbl]),
+            "aqc_set_initial_state": (i32, [vp, i32, u64, vp]),
+            "aqc_propagate": (i32, [vp, i64, C.POINTER(aqc_stats)]),
+            "aqc_get_state": (i32, [vp, vp, i32]),
+            "aqc_fidelity": (i32, [vp, u64, C.POINTER(dbl)]),
+            "aqc_energy": (i32, [vp, i32, C.POINTER(dbl)]),
+            "aqc_norm2": (i32, [vp, C.POINTER(dbl)]),
+            "aqc_hpsi": (i32, [vp, dbl, vp, vp]),
+            "aqc_last_error": (C.c_char_p, [vp]),
+            "aqc_version": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_functions(path: str = HEADER_PATH):
+    """Names of the functions declared in include/aqc.h."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(aqc_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _check(ctx, rc):
+    if rc != AQC_OK:
+        msg = lib().aqc_last_error(ctx)
+        raise AqcError(rc, msg.decode() if msg else "")
+    return rc
+
+
+# ---- thin wrappers under the C names ---------------------------------------------------
+def aqc_workspace_bytes(n_qubits: int, precision: int) -> int:
+    return int(lib().aqc_workspace_bytes(n_qubits, precision))
+
+
+def aqc_create(device: int, precision: int, n_qubits: int, workspace: int, workspace_bytes: int, stream: int):
+    h = C.c_void_p()
+    rc = lib().aqc_create(C.byref(h), device, precision, n_qubits, C.c_void_p(workspace), workspace_bytes,
+                          C.c_void_p(stream))
+    _check(None, rc)
+    return h
+
+
+def aqc_destroy(ctx):
+    lib().aqc_destroy(ctx)
+
+
+def aqc_set_stream(ctx, stream: int):
+    _check(ctx, lib().aqc_set_stream(ctx, C.c_void_p(stream)))
+
+
+def aqc_load_terms(ctx, group, n_terms, xmask_ptr, zmask_ptr, coef_ptr):
+    _check(ctx, lib().aqc_load_terms(ctx, group, n_terms, xmask_ptr, zmask_ptr, coef_ptr))
+
+
+def aqc_load_clauses(ctx, group, m, bits_ptr, penalty, scale):
+    _check(ctx, lib().aqc_load_clauses(ctx, group, m, bits_ptr, penalty, float(scale)))
+
+
+def aqc_clear_hamiltonian(ctx):
+    _check(ctx, lib().aqc_clear_hamiltonian(ctx))
+
+
+def aqc_set_schedule(ctx, s_kind, T, coefA, coefB, coefC):
+    arr = [(C.c_double * 4)(*[float(v) for v in c]) for c in (coefA, coefB, coefC)]
+    _check(ctx, lib().aqc_set_schedule(ctx, s_kind, float(T), arr[0], arr[1], arr[2]))
+
+
+def aqc_set_integrator(ctx, n_steps, kappa):
+    _check(ctx, lib().aqc_set_integrator(ctx, int(n_steps), float(kappa)))
+
+
+def aqc_set_initial_state(ctx, kind, basis, user_ptr):
+    _check(ctx, lib().aqc_set_initial_state(ctx, kind, int(basis), C.c_void_p(user_ptr) if user_ptr else None))
+
+
+def aqc_propagate(ctx, max_steps, want_stats=True):
+    st = aqc_stats()
+    _check(ctx, lib().aqc_propagate(ctx, int(max_steps), C.byref(st) if want_stats else None))
+    return st.as_dict() if want_stats else None
+
+
+def aqc_get_state(ctx, dst_ptr, dst_on_device):
+    _check(ctx, lib().aqc_get_state(ctx, C.c_void_p(dst_ptr), int(dst_on_device)))
+
+
+def aqc_fidelity(ctx, w):
+    out = C.c_double()
+    _check(ctx, lib().aqc_fidelity(ctx, int(w), C.byref(out)))
+    return out.value
+
+
+def aqc_energy(ctx, group):
+    out = C.c_double()
+    _check(ctx, lib().aqc_energy(ctx, int(group), C.byref(out)))
+    return out.value
+
+
+def aqc_norm2(ctx):
+    out = C.c_double()
+    _check(ctx, lib().aqc_norm2(ctx, C.byref(out)))
+    return out.value
+
+
+def aqc_hpsi(ctx, t, psi_ptr, out_ptr):
+    _check(ctx, lib().aqc_hpsi(ctx, float(t), C.c_void_p(psi_ptr), C.c_void_p(out_ptr)))
+
+
+def aqc_last_error(ctx):
+    m = lib().aqc_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def aqc_version():
+    return lib().aqc_version().decode()

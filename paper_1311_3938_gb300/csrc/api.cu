@@ -1,0 +1,721 @@
+// C ABI (include/aqc.h): context, SQH term packing, layouts, schedule, step rule and the
+// integrator driver (RK4 start-up, then one fused PEC kernel chain per step).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/aqc.h"
+#include "aqc_internal.h"
+
+using namespace aqc;
+
+namespace {
+
+enum { V_Y = 0, V_P = 1, V_Q = 2, V_F0 = 3, V_ACC = 7, V_COUNT = 8 };
+
+struct TermH {
+  uint32_t x, zm;
+  double coef;
+  int group;
+};
+struct ClauseH {
+  uint32_t mask;
+  int group, pen;
+  double scale;
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int tile_bits_max(int prec) { return prec == AQC_C128 ? 12 : 13; }
+int chunk_bits(int prec) { return prec == AQC_C128 ? 4 : 5; }  // 256-byte contiguous chunks
+
+std::vector<Layout> layouts_for(int n, int prec) {
+  std::vector<Layout> ls;
+  const int tmax = tile_bits_max(prec), cc = chunk_bits(prec);
+  if (n <= tmax) {
+    ls.push_back(Layout{n, n, 0, n});
+    return ls;
+  }
+  ls.push_back(Layout{tmax, tmax, 0, tmax});
+  int start = tmax;
+  while (start < n) {
+    const int w = std::min(tmax - cc, n - start);
+    ls.push_back(Layout{cc, start, w, cc + w});
+    start += w;
+  }
+  return ls;
+}
+
+size_t max_tiles(int n, int prec) {
+  size_t g = 1;
+  for (const Layout& L : layouts_for(n, prec)) g = std::max(g, (size_t)1 << (n - L.t));
+  return g;
+}
+
+struct WsPlan {
+  size_t off_tab, off_slots, off_counter, off_partials, off_vec, vec_bytes, total;
+  size_t partial_doubles;
+};
+
+WsPlan plan_workspace(int n, int prec) {
+  WsPlan w;
+  const size_t amp = prec == AQC_C128 ? 16 : 8;
+  w.off_tab = 0;
+  w.off_slots = align_up(sizeof(DevTables), 256);
+  w.off_counter = w.off_slots + 256;
+  w.off_partials = w.off_counter + 256;
+  size_t g = std::max(max_tiles(n, prec), (size_t)reduce_grid((uint64_t)1 << n));
+  w.partial_doubles = 3 * g;
+  w.off_vec = align_up(w.off_partials + w.partial_doubles * sizeof(double), 256);
+  w.vec_bytes = align_up(((size_t)1 << n) * amp, 256);
+  w.total = w.off_vec + V_COUNT * w.vec_bytes;
+  return w;
+}
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct aqc_ctx {
+  int device = 0, prec = 0, n = 0;
+  uint64_t N = 0;
+  size_t amp = 0;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  WsPlan wp;
+  void* vec[V_COUNT];
+  DevTables* d_tab = nullptr;
+  double* d_slots = nullptr;
+  unsigned* d_counter = nullptr;
+  double* d_partials = nullptr;
+  DevTables* h_tab = nullptr;
+
+  std::vector<TermH> terms;
+  std::vector<ClauseH> clauses;
+  bool dirty = true;
+  std::vector<Layout> layouts;
+  std::vector<int> nflips;  // local flips per layout
+  int n_remote = 0, n_z = 0;
+
+  bool have_sched = false;
+  int s_kind = 0;
+  double T = 0;
+  double poly[3][4];
+  int64_t nsteps_req = 0;
+  double kappa = 0.1;
+
+  bool have_state = false;
+  bool hist_ready = false;
+  int64_t step = 0, nsteps = 0, evals = 0;
+  double h = 0;
+
+  std::string err;
+};
+
+#define FAIL(ctx, code, ...)                                     \
+  do {                                                           \
+    char buf_[512];                                              \
+    snprintf(buf_, sizeof(buf_), __VA_ARGS__);                   \
+    (ctx)->err = buf_;                                           \
+    return (code);                                               \
+  } while (0)
+
+#define CUDA_TRY(ctx, expr)                                                                  \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) FAIL(ctx, AQC_E_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+uint32_t layout_mask(const Layout& L) {
+  uint32_t m = L.c >= 32 ? 0xffffffffu : ((1u << L.c) - 1u);
+  if (L.w > 0) m |= ((1u << L.w) - 1u) << L.h;
+  return m;
+}
+
+uint32_t compress_mask(const Layout& L, uint32_t x) {
+  uint32_t r = 0;
+  for (int g = 0; g < 32; g++) {
+    if (!((x >> g) & 1u)) continue;
+    if (g < L.c)
+      r |= 1u << g;
+    else
+      r |= 1u << (L.c + (g - L.h));
+  }
+  return r;
+}
+
+void plan_layouts(aqc_ctx* c) { c->layouts = layouts_for(c->n, c->prec); }
+
+int build_tables(aqc_ctx* c) {
+  plan_layouts(c);
+  DevTables* t = c->h_tab;
+  memset(t, 0, sizeof(DevTables));
+  const int nl = (int)c->layouts.size();
+  if (nl > kMaxLayouts) FAIL(c, AQC_E_UNSUPPORTED, "too many layouts (%d)", nl);
+  t->n_layouts = nl;
+  std::vector<std::vector<DevFlip>> per(nl + 1);
+  int nz = 0;
+  for (const TermH& th : c->terms) {
+    if (th.x == 0) {
+      if (th.zm == 0) {
+        t->ident[th.group] += th.coef;
+      } else {
+        if (nz >= kMaxZ) FAIL(c, AQC_E_UNSUPPORTED, "more than %d diagonal Pauli products", kMaxZ);
+        t->z[nz].zm = th.zm;
+        t->z[nz].group = th.group;
+        t->z[nz].coef = th.coef;
+        nz++;
+      }
+      continue;
+    }
+    DevFlip f;
+    memset(&f, 0, sizeof(f));
+    f.x = th.x;
+    f.zm = th.zm;
+    f.group = th.group;
+    f.ipow = __builtin_popcount(th.x & th.zm) & 3;
+    f.coef = th.coef;
+    int where = nl;
+    for (int l = 0; l < nl; l++) {
+      if ((th.x & ~layout_mask(c->layouts[l])) == 0) {
+        where = l;
+        break;
+      }
+    }
+    f.lx = where < nl ? compress_mask(c->layouts[where], th.x) : 0u;
+    per[where].push_back(f);
+  }
+  int pos = 0;
+  c->nflips.assign(nl, 0);
+  for (int l = 0; l <= nl; l++) {
+    t->flip_begin[l] = pos;
+    if (pos + (int)per[l].size() > kMaxFlips) FAIL(c, AQC_E_UNSUPPORTED, "more than %d off-diagonal products", kMaxFlips);
+    for (const DevFlip& f : per[l]) t->flips[pos++] = f;
+    if (l < nl) c->nflips[l] = (int)per[l].size();
+  }
+  t->flip_begin[nl + 1] = pos;
+  t->n_remote = (int)per[nl].size();
+  c->n_remote = t->n_remote;
+  t->n_z = nz;
+  c->n_z = nz;
+  // clause classes (group, penalty, scale), clauses sorted by class in first-seen order
+  std::vector<ClauseH> cl = c->clauses;
+  std::vector<int> cls_of(cl.size());
+  std::vector<DevClass> classes;
+  for (size_t i = 0; i < cl.size(); i++) {
+    int k = -1;
+    for (size_t j = 0; j < classes.size(); j++)
+      if (classes[j].group == cl[i].group && classes[j].pen == cl[i].pen && classes[j].scale == cl[i].scale) k = (int)j;
+    if (k < 0) {
+      if ((int)classes.size() >= kMaxClasses) FAIL(c, AQC_E_UNSUPPORTED, "more than %d clause classes", kMaxClasses);
+      DevClass dc;
+      memset(&dc, 0, sizeof(dc));
+      dc.group = cl[i].group;
+      dc.pen = cl[i].pen;
+      dc.scale = cl[i].scale;
+      classes.push_back(dc);
+      k = (int)classes.size() - 1;
+    }
+    cls_of[i] = k;
+  }
+  if ((int)cl.size() > kMaxClauses) FAIL(c, AQC_E_UNSUPPORTED, "more than %d clauses", kMaxClauses);
+  int cp = 0;
+  for (size_t k = 0; k < classes.size(); k++) {
+    classes[k].begin = cp;
+    for (size_t i = 0; i < cl.size(); i++)
+      if (cls_of[i] == (int)k) t->clause_mask[cp++] = cl[i].mask;
+    classes[k].end = cp;
+    t->classes[k] = classes[k];
+  }
+  t->n_classes = (int)classes.size();
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_tab, t, sizeof(DevTables), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->dirty = false;
+  return AQC_OK;
+}
+
+void sched_weights(const aqc_ctx* c, double t, double w[3]) {
+  const double tau = t / c->T;
+  const double s = c->s_kind == AQC_S_SMOOTHSTEP ? tau * tau * (3.0 - 2.0 * tau) : tau;
+  for (int g = 0; g < 3; g++) w[g] = ((c->poly[g][3] * s + c->poly[g][2]) * s + c->poly[g][1]) * s + c->poly[g][0];
+}
+
+double group_bound(const aqc_ctx* c, int g) {
+  double b = 0.0;
+  for (const TermH& t : c->terms)
+    if (t.group == g) b += fabs(t.coef);
+  for (const ClauseH& k : c->clauses)
+    if (k.group == g) b += fabs(k.scale) * (k.pen == AQC_PEN_SQUARED ? 4.0 : 1.0);
+  return b;
+}
+
+int64_t rule_steps(const aqc_ctx* c) {
+  double b[3];
+  for (int g = 0; g < 3; g++) b[g] = group_bound(c, g);
+  double lam = 0.0;
+  for (int i = 0; i <= 1024; i++) {
+    const double s = i / 1024.0;
+    double v = 0.0;
+    for (int g = 0; g < 3; g++) {
+      const double wg = ((c->poly[g][3] * s + c->poly[g][2]) * s + c->poly[g][1]) * s + c->poly[g][0];
+      v += fabs(wg) * b[g];
+    }
+    lam = std::max(lam, v);
+  }
+  const double n = ceil(c->T * lam / c->kappa);
+  return std::max<int64_t>(4, (int64_t)n);
+}
+
+ApplyParams base_params(aqc_ctx* c) {
+  ApplyParams p;
+  memset(&p, 0, sizeof(p));
+  p.tab = c->d_tab;
+  p.n = c->n;
+  p.partials = c->d_partials;
+  p.counter = c->d_counter;
+  p.slots = c->d_slots;
+  return p;
+}
+
+// One evaluation of H(t) src over all layouts; the last layout runs the mode epilogue.
+int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, void* partial_out) {
+  const int nl = (int)c->layouts.size();
+  for (int l = 0; l < nl; l++) {
+    ApplyParams p = (l == nl - 1) ? fin : base_params(c);
+    p.L = c->layouts[l];
+    p.layout_index = l;
+    p.with_diag = (l == 0);
+    p.with_remote = (l == 0);
+    for (int g = 0; g < 3; g++) p.w[g] = w[g];
+    p.src = src;
+    p.qin = (l == 0) ? nullptr : c->vec[V_Q];
+    if (l < nl - 1) {
+      p.mode = MODE_PARTIAL;
+      p.qout = c->vec[V_Q];
+    } else if (fin.mode == MODE_PARTIAL) {
+      p.qout = partial_out;
+    }
+    const int grid = 1 << (c->n - p.L.t);
+    const size_t smem = apply_smem_bytes(c->prec, p.L.t, c->nflips[l], l == 0 ? c->n_remote : 0, l == 0 ? c->n_z : 0);
+    if (smem > 227 * 1024) FAIL(c, AQC_E_UNSUPPORTED, "shared memory %zu bytes too large", smem);
+    CUDA_TRY(c, launch_apply(c->prec, p, grid, (int)smem, c->stream));
+  }
+  return AQC_OK;
+}
+
+int ensure_ready(aqc_ctx* c) {
+  if (!c->have_sched) FAIL(c, AQC_E_STATE, "no schedule set");
+  if (c->dirty) {
+    int rc = build_tables(c);
+    if (rc) return rc;
+  }
+  return AQC_OK;
+}
+
+int rk4_step(aqc_ctx* c) {
+  const double t = (double)c->step * c->h, hh = c->h;
+  double w[3];
+  for (int stage = 1; stage <= 4; stage++) {
+    const double ts = stage == 1 ? t : (stage == 4 ? t + hh : t + 0.5 * hh);
+    sched_weights(c, ts, w);
+    ApplyParams fin = base_params(c);
+    fin.mode = MODE_RK4;
+    fin.stage = stage;
+    fin.h = hh;
+    fin.y = c->vec[V_Y];
+    fin.acc = c->vec[V_ACC];
+    fin.pout = c->vec[V_P];
+    fin.fout = c->vec[V_F0 + (int)(c->step & 3)];
+    int rc = evaluate(c, w, stage == 1 ? c->vec[V_Y] : c->vec[V_P], fin, nullptr);
+    if (rc) return rc;
+    c->evals++;
+  }
+  c->step++;
+  return AQC_OK;
+}
+
+int start_history(aqc_ctx* c) {
+  // f_3 = -i H(t_3) y_3, then p_4 from the AB4 predictor
+  double w[3];
+  sched_weights(c, 3.0 * c->h, w);
+  ApplyParams fin = base_params(c);
+  fin.mode = MODE_DERIV;
+  fin.fout = c->vec[V_F0 + 3];
+  int rc = evaluate(c, w, c->vec[V_Y], fin, nullptr);
+  if (rc) return rc;
+  c->evals++;
+  CUDA_TRY(c, launch_predict(c->prec, c->vec[V_P], c->vec[V_Y], c->vec[V_F0 + 3], c->vec[V_F0 + 2],
+                             c->vec[V_F0 + 1], c->vec[V_F0 + 0], c->h, c->N, c->stream));
+  c->hist_ready = true;
+  return AQC_OK;
+}
+
+int pec_step(aqc_ctx* c) {
+  const int64_t n = c->step;
+  double w[3];
+  sched_weights(c, (double)(n + 1) * c->h, w);
+  ApplyParams fin = base_params(c);
+  fin.mode = MODE_STEP;
+  fin.h = c->h;
+  fin.y = c->vec[V_Y];
+  fin.f0 = c->vec[V_F0 + (int)(n & 3)];
+  fin.f1 = c->vec[V_F0 + (int)((n - 1) & 3)];
+  fin.f2 = c->vec[V_F0 + (int)((n - 2) & 3)];
+  fin.fout = c->vec[V_F0 + (int)((n + 1) & 3)];
+  fin.pout = c->vec[V_P];
+  int rc = evaluate(c, w, c->vec[V_P], fin, nullptr);
+  if (rc) return rc;
+  c->evals++;
+  c->step++;
+  return AQC_OK;
+}
+
+int read_slot(aqc_ctx* c, int slot, double* out) {
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->d_slots + slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return AQC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t aqc_workspace_bytes(int n_qubits, int precision) {
+  if (n_qubits < 1 || n_qubits > kMaxN) return 0;
+  if (precision != AQC_C128 && precision != AQC_C64) return 0;
+  return plan_workspace(n_qubits, precision).total;
+}
+
+int aqc_create(aqc_ctx** out, int device, int precision, int n_qubits, void* workspace, size_t workspace_bytes,
+               void* cuda_stream) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return AQC_E_INVAL;
+  }
+  *out = nullptr;
+  if (n_qubits < 1 || n_qubits > kMaxN || (precision != AQC_C128 && precision != AQC_C64)) {
+    g_create_error = "n_qubits must be in [1, 31] and precision AQC_C128 or AQC_C64";
+    return AQC_E_INVAL;
+  }
+  const WsPlan wp = plan_workspace(n_qubits, precision);
+  if (!workspace || workspace_bytes < wp.total) {
+    g_create_error = "workspace missing or smaller than aqc_workspace_bytes()";
+    return AQC_E_NOMEM;
+  }
+  if (((uintptr_t)workspace) & 255u) {
+    g_create_error = "workspace must be 256-byte aligned";
+    return AQC_E_INVAL;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    g_create_error = "no such CUDA device";
+    return AQC_E_CUDA;
+  }
+  aqc_ctx* c = new (std::nothrow) aqc_ctx();
+  if (!c) {
+    g_create_error = "host allocation failed";
+    return AQC_E_NOMEM;
+  }
+  c->h_tab = new (std::nothrow) DevTables();
+  if (!c->h_tab) {
+    delete c;
+    g_create_error = "host allocation failed";
+    return AQC_E_NOMEM;
+  }
+  c->device = device;
+  c->prec = precision;
+  c->n = n_qubits;
+  c->N = (uint64_t)1 << n_qubits;
+  c->amp = precision == AQC_C128 ? 16 : 8;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->ws = (char*)workspace;
+  c->wp = wp;
+  c->d_tab = (DevTables*)(c->ws + wp.off_tab);
+  c->d_slots = (double*)(c->ws + wp.off_slots);
+  c->d_counter = (unsigned*)(c->ws + wp.off_counter);
+  c->d_partials = (double*)(c->ws + wp.off_partials);
+  for (int v = 0; v < V_COUNT; v++) c->vec[v] = c->ws + wp.off_vec + (size_t)v * wp.vec_bytes;
+  for (int g = 0; g < 3; g++)
+    for (int k = 0; k < 4; k++) c->poly[g][k] = 0.0;
+  DeviceGuard dg(device);
+  if (cudaMemsetAsync(c->ws + wp.off_slots, 0, 512, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    g_create_error = "cudaMemsetAsync on the workspace failed";
+    delete c->h_tab;
+    delete c;
+    return AQC_E_CUDA;
+  }
+  *out = c;
+  return AQC_OK;
+}
+
+void aqc_destroy(aqc_ctx* ctx) {
+  if (!ctx) return;
+  delete ctx->h_tab;
+  delete ctx;
+}
+
+int aqc_set_stream(aqc_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return AQC_E_INVAL;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return AQC_OK;
+}
+
+int aqc_load_terms(aqc_ctx* ctx, int group, size_t n_terms, const uint64_t* xmask, const uint64_t* zmask,
+                   const double* coef) {
+  if (!ctx) return AQC_E_INVAL;
+  if (group < 0 || group > 2) FAIL(ctx, AQC_E_INVAL, "group must be 0, 1 or 2");
+  if (n_terms && (!xmask || !zmask || !coef)) FAIL(ctx, AQC_E_INVAL, "NULL term array");
+  const uint64_t lim = ctx->N;
+  for (size_t k = 0; k < n_terms; k++) {
+    if (xmask[k] >= lim || zmask[k] >= lim) FAIL(ctx, AQC_E_INVAL, "term %zu: mask >= 2^n", k);
+    if (!isfinite(coef[k])) FAIL(ctx, AQC_E_INVAL, "term %zu: non-finite coefficient", k);
+  }
+  for (size_t k = 0; k < n_terms; k++) ctx->terms.push_back(TermH{(uint32_t)xmask[k], (uint32_t)zmask[k], coef[k], group});
+  ctx->dirty = true;
+  return AQC_OK;
+}
+
+int aqc_load_clauses(aqc_ctx* ctx, int group, size_t m, const int32_t* bits, int penalty, double scale) {
+  if (!ctx) return AQC_E_INVAL;
+  if (group < 0 || group > 2) FAIL(ctx, AQC_E_INVAL, "group must be 0, 1 or 2");
+  if (penalty != AQC_PEN_INDICATOR && penalty != AQC_PEN_SQUARED) FAIL(ctx, AQC_E_INVAL, "bad penalty kind");
+  if (!isfinite(scale)) FAIL(ctx, AQC_E_INVAL, "non-finite scale");
+  if (m && !bits) FAIL(ctx, AQC_E_INVAL, "NULL clause array");
+  for (size_t k = 0; k < m; k++) {
+    const int a = bits[3 * k], b = bits[3 * k + 1], d = bits[3 * k + 2];
+    if (a < 0 || b < 0 || d < 0 || a >= ctx->n || b >= ctx->n || d >= ctx->n || a == b || b == d || a == d)
+      FAIL(ctx, AQC_E_INVAL, "clause %zu: bits must be distinct and < n", k);
+  }
+  for (size_t k = 0; k < m; k++) {
+    const uint32_t mask = (1u << bits[3 * k]) | (1u << bits[3 * k + 1]) | (1u << bits[3 * k + 2]);
+    ctx->clauses.push_back(ClauseH{mask, group, penalty, scale});
+  }
+  ctx->dirty = true;
+  return AQC_OK;
+}
+
+int aqc_clear_hamiltonian(aqc_ctx* ctx) {
+  if (!ctx) return AQC_E_INVAL;
+  ctx->terms.clear();
+  ctx->clauses.clear();
+  ctx->dirty = true;
+  return AQC_OK;
+}
+
+int aqc_set_schedule(aqc_ctx* ctx, int s_kind, double T, const double coefA[4], const double coefB[4],
+                     const double coefC[4]) {
+  if (!ctx) return AQC_E_INVAL;
+  if (s_kind != AQC_S_LINEAR && s_kind != AQC_S_SMOOTHSTEP) FAIL(ctx, AQC_E_INVAL, "bad s_kind");
+  if (!(T > 0.0) || !isfinite(T)) FAIL(ctx, AQC_E_INVAL, "T must be positive and finite");
+  const double* cs[3] = {coefA, coefB, coefC};
+  for (int g = 0; g < 3; g++)
+    for (int k = 0; k < 4; k++) {
+      const double v = cs[g] ? cs[g][k] : 0.0;
+      if (!isfinite(v)) FAIL(ctx, AQC_E_INVAL, "non-finite schedule coefficient");
+      ctx->poly[g][k] = v;
+    }
+  ctx->s_kind = s_kind;
+  ctx->T = T;
+  ctx->have_sched = true;
+  ctx->have_state = false;  // a new schedule restarts the integration
+  return AQC_OK;
+}
+
+int aqc_set_integrator(aqc_ctx* ctx, int64_t n_steps, double kappa) {
+  if (!ctx) return AQC_E_INVAL;
+  if (n_steps < 0) FAIL(ctx, AQC_E_INVAL, "n_steps must be >= 0");
+  if (kappa < 0.0 || !isfinite(kappa)) FAIL(ctx, AQC_E_INVAL, "kappa must be >= 0");
+  ctx->nsteps_req = n_steps;
+  ctx->kappa = kappa > 0.0 ? kappa : 0.1;
+  ctx->have_state = false;
+  return AQC_OK;
+}
+
+int aqc_set_initial_state(aqc_ctx* ctx, int kind, uint64_t basis, const void* user) {
+  if (!ctx) return AQC_E_INVAL;
+  DeviceGuard dg(ctx->device);
+  void* y = ctx->vec[V_Y];
+  const size_t bytes = (size_t)ctx->N * ctx->amp;
+  switch (kind) {
+    case AQC_INIT_UNIFORM:
+      CUDA_TRY(ctx, launch_init(ctx->prec, y, ctx->N, 0, 0, ctx->stream));
+      break;
+    case AQC_INIT_BASIS:
+      if (basis >= ctx->N) FAIL(ctx, AQC_E_INVAL, "basis index >= 2^n");
+      CUDA_TRY(ctx, launch_init(ctx->prec, y, ctx->N, 1, basis, ctx->stream));
+      break;
+    case AQC_INIT_USER_HOST:
+      if (!user) FAIL(ctx, AQC_E_INVAL, "user vector is NULL");
+      CUDA_TRY(ctx, cudaMemcpyAsync(y, user, bytes, cudaMemcpyHostToDevice, ctx->stream));
+      break;
+    case AQC_INIT_USER_DEVICE:
+      if (!user) FAIL(ctx, AQC_E_INVAL, "user vector is NULL");
+      CUDA_TRY(ctx, cudaMemcpyAsync(y, user, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      break;
+    default:
+      FAIL(ctx, AQC_E_INVAL, "bad initial-state kind");
+  }
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_slots, 0, kSlotCount * sizeof(double), ctx->stream));
+  ctx->step = 0;
+  ctx->evals = 0;
+  ctx->nsteps = 0;
+  ctx->hist_ready = false;
+  ctx->have_state = true;
+  return AQC_OK;
+}
+
+int aqc_propagate(aqc_ctx* ctx, int64_t max_steps, aqc_stats* stats) {
+  if (!ctx) return AQC_E_INVAL;
+  if (!ctx->have_state) FAIL(ctx, AQC_E_STATE, "no initial state (or schedule/integrator changed since)");
+  DeviceGuard dg(ctx->device);
+  int rc = ensure_ready(ctx);
+  if (rc) return rc;
+  if (ctx->nsteps == 0) {
+    ctx->nsteps = ctx->nsteps_req > 0 ? ctx->nsteps_req : rule_steps(ctx);
+    ctx->h = ctx->T / (double)ctx->nsteps;
+  }
+  const int64_t target = max_steps < 0 ? ctx->nsteps : std::min(ctx->nsteps, ctx->step + max_steps);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (stats) {
+    CUDA_TRY(ctx, cudaEventCreate(&e0));
+    CUDA_TRY(ctx, cudaEventCreate(&e1));
+    CUDA_TRY(ctx, cudaEventRecord(e0, ctx->stream));
+  }
+  while (ctx->step < target) {
+    if (ctx->step < 3) {
+      rc = rk4_step(ctx);
+    } else {
+      if (!ctx->hist_ready) {
+        rc = start_history(ctx);
+        if (rc) break;
+      }
+      rc = pec_step(ctx);
+    }
+    if (rc) break;
+  }
+  if (stats) {
+    cudaEventRecord(e1, ctx->stream);
+    if (!rc) {
+      memset(stats, 0, sizeof(*stats));
+      stats->steps_done = ctx->step;
+      stats->n_steps = ctx->nsteps;
+      stats->evaluations = ctx->evals;
+      stats->h = ctx->h;
+      stats->t = (double)ctx->step * ctx->h;
+      cudaError_t e = launch_reduce(ctx->prec, 0, ctx->vec[V_Y], ctx->N, ctx->d_partials, ctx->d_counter,
+                                    ctx->d_slots, reduce_grid(ctx->N), ctx->stream);
+      double sl[kSlotCount];
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sl, ctx->d_slots, sizeof(sl), cudaMemcpyDeviceToHost, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        ctx->err = std::string("stats readback: ") + cudaGetErrorString(e);
+        rc = AQC_E_CUDA;
+      } else {
+        stats->norm2 = sl[kSlotNorm2];
+        stats->max_err_est = sl[kSlotMaxErr];
+        stats->last_err_est = sl[kSlotLastErr];
+        stats->elapsed_ms = ms;
+        if (!isfinite(sl[kSlotNorm2])) {
+          ctx->err = "non-finite state norm";
+          rc = AQC_E_NUMERIC;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  return rc;
+}
+
+int aqc_get_state(aqc_ctx* ctx, void* dst, int dst_on_device) {
+  if (!ctx) return AQC_E_INVAL;
+  if (!dst) FAIL(ctx, AQC_E_INVAL, "dst is NULL");
+  DeviceGuard dg(ctx->device);
+  CUDA_TRY(ctx, cudaMemcpyAsync(dst, ctx->vec[V_Y], (size_t)ctx->N * ctx->amp,
+                                dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return AQC_OK;
+}
+
+int aqc_fidelity(aqc_ctx* ctx, uint64_t w, double* out) {
+  if (!ctx || !out) return AQC_E_INVAL;
+  if (w >= ctx->N) FAIL(ctx, AQC_E_INVAL, "w >= 2^n");
+  DeviceGuard dg(ctx->device);
+  CUDA_TRY(ctx, launch_fidelity(ctx->prec, ctx->vec[V_Y], w, ctx->d_slots, ctx->stream));
+  return read_slot(ctx, kSlotDot, out);
+}
+
+int aqc_energy(aqc_ctx* ctx, int group, double* out) {
+  if (!ctx || !out) return AQC_E_INVAL;
+  if (group < 0 || group > 2) FAIL(ctx, AQC_E_INVAL, "group must be 0, 1 or 2");
+  DeviceGuard dg(ctx->device);
+  if (ctx->dirty) {
+    int rc = build_tables(ctx);
+    if (rc) return rc;
+  }
+  double w[3] = {0.0, 0.0, 0.0};
+  w[group] = 1.0;
+  ApplyParams fin = base_params(ctx);
+  fin.mode = MODE_ENERGY;
+  int rc = evaluate(ctx, w, ctx->vec[V_Y], fin, nullptr);
+  if (rc) return rc;
+  return read_slot(ctx, kSlotDot, out);
+}
+
+int aqc_norm2(aqc_ctx* ctx, double* out) {
+  if (!ctx || !out) return AQC_E_INVAL;
+  DeviceGuard dg(ctx->device);
+  CUDA_TRY(ctx, launch_reduce(ctx->prec, 0, ctx->vec[V_Y], ctx->N, ctx->d_partials, ctx->d_counter, ctx->d_slots,
+                              reduce_grid(ctx->N), ctx->stream));
+  return read_slot(ctx, kSlotNorm2, out);
+}
+
+int aqc_hpsi(aqc_ctx* ctx, double t, const void* psi, void* out) {
+  if (!ctx) return AQC_E_INVAL;
+  if (!psi || !out || psi == out) FAIL(ctx, AQC_E_INVAL, "psi and out must be distinct device pointers");
+  if (!ctx->have_sched) FAIL(ctx, AQC_E_STATE, "no schedule set");
+  DeviceGuard dg(ctx->device);
+  if (ctx->dirty) {
+    int rc = build_tables(ctx);
+    if (rc) return rc;
+  }
+  double w[3];
+  sched_weights(ctx, t, w);
+  ApplyParams fin = base_params(ctx);
+  fin.mode = MODE_PARTIAL;
+  return evaluate(ctx, w, psi, fin, out);
+}
+
+const char* aqc_last_error(const aqc_ctx* ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->err.c_str();
+}
+
+const char* aqc_version(void) { return "aqc-gb300 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// Internal declarations shared by the host driver (api.cu) and the kernels (kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace aqc {
+
+constexpr int kMaxFlips = 2048;   // off-diagonal Pauli products over all layouts
+constexpr int kMaxZ = 1024;       // diagonal Pauli products (Z strings)
+constexpr int kMaxClauses = 1024; // EC3 clauses
+constexpr int kMaxClasses = 8;    // (group, penalty kind, scale) classes of clauses
+constexpr int kMaxLayouts = 8;
+constexpr int kMaxN = 31;
+
+// One off-diagonal Pauli product in gather form: (P psi)(z) = i^ipow (-1)^{|zm & (z^x)|} psi(z^x).
+struct DevFlip {
+  uint32_t x;      // global flip mask
+  uint32_t lx;     // the same mask in tile-local bits of its layout (0 for remote terms)
+  uint32_t zm;     // Z/Y positions (sign from the source index z^x)
+  int32_t group;   // weight slot A/B/C
+  int32_t ipow;    // |x & zm| mod 4 (Y = i X Z)
+  int32_t pad;
+  double coef;
+};
+
+struct DevZ {      // diagonal product coef (-1)^{|zm & z|}
+  uint32_t zm;
+  int32_t group;
+  double coef;
+};
+
+struct DevClass {  // clauses [begin, end) share group, penalty and scale
+  int32_t group;
+  int32_t pen;     // 0 indicator [k != 1], 1 squared (1-k)^2
+  int32_t begin, end;
+  double scale;
+};
+
+// Tile layout: tile bits are [0, c) and [h, h + w); t = c + w; remaining bits index tiles.
+struct Layout {
+  int c, h, w, t;
+};
+
+struct DevTables {
+  int n_layouts;
+  int n_remote;                     // flips no layout holds, gathered from global memory
+  int flip_begin[kMaxLayouts + 2];  // layout l: [flip_begin[l], flip_begin[l+1]); remote after
+  int n_z;
+  int n_classes;
+  int pad[2];
+  double ident[3];                  // identity prefactors per group (energy shifts m^(0))
+  DevClass classes[kMaxClasses];
+  uint32_t clause_mask[kMaxClauses];
+  DevZ z[kMaxZ];
+  DevFlip flips[kMaxFlips];
+};
+
+enum Mode : int {
+  MODE_PARTIAL = 0,  // qout = qin + [diag + remote] + local flips
+  MODE_STEP = 1,     // f_{n+1} = -i(...); PEC corrector + next predictor + reductions
+  MODE_RK4 = 2,      // RK4 stage (stage 1..4)
+  MODE_DERIV = 3,    // fout = -i(...)
+  MODE_ENERGY = 4,   // reduce Re <src| (...) >
+};
+
+struct ApplyParams {
+  const DevTables* tab;
+  int n;
+  Layout L;
+  int layout_index;
+  int with_diag;
+  int with_remote;
+  int mode;
+  int stage;         // RK4 stage 1..4
+  double w[3];       // group weights A, B, C at the evaluation time
+  double h;
+  const void* src;   // vector the Hamiltonian acts on
+  const void* qin;   // partial sum from earlier layouts (nullable)
+  void* qout;        // PARTIAL: output partial sum
+  void* y;           // STEP: y_n -> y_{n+1};  RK4: y (stage 4 writes y)
+  const void* f0;    // STEP: f_n
+  const void* f1;    // STEP: f_{n-1}
+  const void* f2;    // STEP: f_{n-2}
+  void* fout;        // STEP: f_{n+1};  DERIV: f;  RK4 stage 1: history f_n
+  void* pout;        // STEP: p_{n+2};  RK4: stage input for the next stage (ys)
+  void* acc;         // RK4 accumulator
+  double* partials;  // per-CTA reduction partials (3 doubles per CTA)
+  unsigned* counter; // last-CTA ticket (reset to 0 by the last CTA)
+  double* slots;     // results: see kSlot*
+};
+
+// result slots (doubles) in the workspace
+constexpr int kSlotNorm2 = 0;
+constexpr int kSlotMaxErr = 1;
+constexpr int kSlotLastErr = 2;
+constexpr int kSlotDot = 3;
+constexpr int kSlotDotIm = 4;
+constexpr int kSlotCount = 8;
+
+cudaError_t launch_apply(int prec, const ApplyParams& p, int grid, int smem_bytes, cudaStream_t s);
+size_t apply_smem_bytes(int prec, int t, int n_local_flips, int n_remote, int n_z);
+cudaError_t launch_init(int prec, void* y, uint64_t N, int kind, uint64_t basis, cudaStream_t s);
+cudaError_t launch_predict(int prec, void* p, const void* y, const void* f3, const void* f2, const void* f1,
+                           const void* f0, double h, uint64_t N, cudaStream_t s);
+cudaError_t launch_reduce(int prec, int what, const void* a, uint64_t N, double* partials, unsigned* counter,
+                          double* slots, int grid, cudaStream_t s);
+cudaError_t launch_fidelity(int prec, const void* a, uint64_t w, double* slots, cudaStream_t s);
+int reduce_grid(uint64_t N);
+
+}  // namespace aqc

@@ -1,0 +1,139 @@
+"""Python-side context: a torch-allocated device workspace plus the C-ABI handle.
+
+PyTorch provides only device memory (the workspace tensor) and the CUDA stream; all work is
+done by libaqc.so kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def _dtype(precision):
+    return np.complex128 if precision == N.AQC_C128 else np.complex64
+
+
+def _torch_dtype(precision):
+    return torch.complex128 if precision == N.AQC_C128 else torch.complex64
+
+
+class Context:
+    """One state vector of n qubits on one GPU with its integrator (include/aqc.h)."""
+
+    def __init__(self, n: int, precision: int = N.AQC_C128, device: int = 0, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.n = n
+        self.precision = precision
+        self.device = device
+        self.dev = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
+        self.ws_bytes = N.aqc_workspace_bytes(n, precision)
+        if self.ws_bytes == 0:
+            raise ValueError("unsupported n / precision")
+        # +256 so that the pointer can be aligned
+        self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.dev)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self.handle = N.aqc_create(device, precision, n, self._ws_ptr, self.ws_bytes, self.stream.cuda_stream)
+        self.N = 1 << n
+
+    # ---- lifetime
+    def close(self):
+        if getattr(self, "handle", None):
+            torch.cuda.synchronize(self.dev)
+            N.aqc_destroy(self.handle)
+            self.handle = None
+            self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- Hamiltonian
+    def load_terms(self, group, xmask, zmask, coef):
+        x = np.ascontiguousarray(xmask, dtype=np.uint64)
+        z = np.ascontiguousarray(zmask, dtype=np.uint64)
+        c = np.ascontiguousarray(coef, dtype=np.float64)
+        if not (len(x) == len(z) == len(c)):
+            raise ValueError("term arrays differ in length")
+        N.aqc_load_terms(self.handle, group, len(x), x.ctypes.data, z.ctypes.data, c.ctypes.data)
+
+    def load_clauses(self, group, clauses, penalty=N.AQC_PEN_INDICATOR, scale=1.0):
+        b = np.ascontiguousarray(np.asarray(clauses, dtype=np.int32).reshape(-1))
+        N.aqc_load_clauses(self.handle, group, len(b) // 3, b.ctypes.data, penalty, scale)
+
+    def clear_hamiltonian(self):
+        N.aqc_clear_hamiltonian(self.handle)
+
+    # ---- schedule / integrator
+    def set_schedule(self, T, weights, s_kind=N.AQC_S_LINEAR):
+        N.aqc_set_schedule(self.handle, s_kind, T, *weights)
+
+    def set_integrator(self, n_steps=0, kappa=0.0):
+        N.aqc_set_integrator(self.handle, n_steps, kappa)
+
+    def set_initial_state(self, state="uniform"):
+        if isinstance(state, str) and state == "uniform":
+            N.aqc_set_initial_state(self.handle, N.AQC_INIT_UNIFORM, 0, 0)
+        elif isinstance(state, (int, np.integer)):
+            N.aqc_set_initial_state(self.handle, N.AQC_INIT_BASIS, int(state), 0)
+        elif isinstance(state, torch.Tensor):
+            t = state.to(self.dev, _torch_dtype(self.precision)).contiguous()
+            if t.numel() != self.N:
+                raise ValueError("state has the wrong length")
+            N.aqc_set_initial_state(self.handle, N.AQC_INIT_USER_DEVICE, 0, t.data_ptr())
+            self.stream.synchronize()
+        else:
+            a = np.ascontiguousarray(state, dtype=_dtype(self.precision))
+            if a.size != self.N:
+                raise ValueError("state has the wrong length")
+            N.aqc_set_initial_state(self.handle, N.AQC_INIT_USER_HOST, 0, a.ctypes.data)
+            self.stream.synchronize()
+
+    def propagate(self, max_steps=-1, stats=True):
+        return N.aqc_propagate(self.handle, max_steps, stats)
+
+    # ---- results
+    def state(self, device=False):
+        if device:
+            out = torch.empty(self.N, dtype=_torch_dtype(self.precision), device=self.dev)
+            N.aqc_get_state(self.handle, out.data_ptr(), 1)
+            return out
+        out = np.empty(self.N, dtype=_dtype(self.precision))
+        N.aqc_get_state(self.handle, out.ctypes.data, 0)
+        return out
+
+    def state_into(self, host_tensor):
+        """Copy psi into a (pinned) host torch tensor of the state dtype."""
+        N.aqc_get_state(self.handle, host_tensor.data_ptr(), 0)
+        return host_tensor
+
+    def fidelity(self, w):
+        return N.aqc_fidelity(self.handle, w)
+
+    def energy(self, group=N.AQC_GRP_B):
+        return N.aqc_energy(self.handle, group)
+
+    def norm2(self):
+        return N.aqc_norm2(self.handle)
+
+    def hpsi(self, t, psi: torch.Tensor, out: torch.Tensor = None):
+        """out = H(t) psi for device tensors of the state dtype."""
+        psi = psi.to(self.dev, _torch_dtype(self.precision)).contiguous()
+        if out is None:
+            out = torch.empty_like(psi)
+        N.aqc_hpsi(self.handle, t, psi.data_ptr(), out.data_ptr())
+        return out

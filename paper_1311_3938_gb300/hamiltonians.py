@@ -1,0 +1,85 @@
+"""SQH term lists of the paper's Hamiltonians, as arrays for aqc_load_terms / aqc_load_clauses.
+
+Qubit q of the paper is bit q-1 of the basis index (Eq. ztensor).  All builders return plain
+numpy arrays (xmask uint64, zmask uint64, coef float64) or clause bit triples (int32).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _native as N
+
+# path weights as cubics in s (w(s) = c0 + c1 s + c2 s^2 + c3 s^3)
+W_ONE_MINUS_S = (1.0, -1.0, 0.0, 0.0)
+W_S = (0.0, 1.0, 0.0, 0.0)
+W_ZERO = (0.0, 0.0, 0.0, 0.0)
+
+
+def w_s_one_minus_s(alpha: float = 1.0):
+    """alpha * s (1 - s), the weight of the third path term (Eq. nlpath)."""
+    return (0.0, float(alpha), -float(alpha), 0.0)
+
+
+def x_driver_terms(n: int, weights=None):
+    """Eq. Hix: H^x = sum_i c_i (1 - sigma^x_i); c_i = 1/2 by default (n_i/2 in the paper).
+    Returns the identity prefactor sum c_i and one -c_i sigma^x_i product per qubit."""
+    c = np.full(n, 0.5) if weights is None else np.asarray(weights, dtype=np.float64)
+    x = np.concatenate([[0], 1 << np.arange(n, dtype=np.uint64)]).astype(np.uint64)
+    z = np.zeros(n + 1, dtype=np.uint64)
+    coef = np.concatenate([[c.sum()], -c]).astype(np.float64)
+    return x, z, coef
+
+
+def xx_terms(pairs):
+    """sum_(i,j) J_ij sigma^x_i sigma^x_j over (i, j, J) triples."""
+    x = np.array([(1 << i) | (1 << j) for (i, j, _) in pairs], dtype=np.uint64)
+    z = np.zeros(len(pairs), dtype=np.uint64)
+    coef = np.array([J for (_, _, J) in pairs], dtype=np.float64)
+    return x, z, coef
+
+
+def ec3_zz_terms(n: int, clauses, omega: float = 1.0):
+    """Eq. final_ham: Omega m 1 - Omega sum_i n_i/2 sigma^z_i + Omega sum_{i<j} n_ij/2 sigma^z_i sigma^z_j."""
+    ni = np.zeros(n)
+    nij = {}
+    for c in clauses:
+        for a in c:
+            ni[a] += 1
+        for u in range(3):
+            for v in range(u + 1, 3):
+                key = (min(c[u], c[v]), max(c[u], c[v]))
+                nij[key] = nij.get(key, 0) + 1
+    xs, zs, cs = [0], [0], [omega * len(clauses)]
+    for i in range(n):
+        if ni[i]:
+            xs.append(0)
+            zs.append(1 << i)
+            cs.append(-omega * ni[i] / 2)
+    for (i, j), v in sorted(nij.items()):
+        xs.append(0)
+        zs.append((1 << i) | (1 << j))
+        cs.append(omega * v / 2)
+    return np.array(xs, np.uint64), np.array(zs, np.uint64), np.array(cs, np.float64)
+
+
+def clause_bits(clauses):
+    """EC3 clauses (Eq. 1clause) as a flat int32 array of 0-based bits."""
+    return np.ascontiguousarray(np.array(clauses, dtype=np.int32).reshape(-1))
+
+
+def load_ec3(ctx, inst, pairs=None, penalty=N.AQC_PEN_INDICATOR, x_weights=None):
+    """Load H_i (group A), the clause penalties of H_f (group B) and optional H_c (group C)."""
+    ctx.load_terms(N.AQC_GRP_A, *x_driver_terms(inst.n, x_weights))
+    ctx.load_clauses(N.AQC_GRP_B, inst.clauses, penalty=penalty)
+    if pairs:
+        ctx.load_terms(N.AQC_GRP_C, *xx_terms(pairs))
+
+
+def linear_schedule():
+    """Eq. aqc: A = 1 - s, B = s."""
+    return (W_ONE_MINUS_S, W_S, W_ZERO)
+
+
+def nonlinear_schedule(alpha: float = 1.0):
+    """Eq. nlpath form: A = 1 - s, B = s, C = alpha s (1 - s)."""
+    return (W_ONE_MINUS_S, W_S, w_s_one_minus_s(alpha))

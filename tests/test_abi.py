@@ -1,0 +1,56 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every declared symbol;
+host-only logic (workspace sizing, argument checks before any device call) behaves."""
+import ctypes as C
+import os
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def native():
+    import paper_1311_3938_gb300 as P
+    from paper_1311_3938_gb300 import _native as N
+
+    P.build()
+    N.lib()
+    return N
+
+
+def test_library_exports_every_header_symbol(native):
+    names = native.header_functions()
+    assert len(names) >= 17
+    raw = C.CDLL(native.LIB_PATH)
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_workspace_bytes(native):
+    for prec, amp in ((0, 16), (1, 8)):
+        for n in (1, 10, 20, 28):
+            b = native.aqc_workspace_bytes(n, prec)
+            assert b >= 8 * (1 << n) * amp
+            assert b < 8 * (1 << n) * amp + 64 * 1024 * 1024
+    assert native.aqc_workspace_bytes(0, 0) == 0
+    assert native.aqc_workspace_bytes(32, 0) == 0
+    assert native.aqc_workspace_bytes(10, 7) == 0
+
+
+def test_create_rejects_bad_arguments(native):
+    h = C.c_void_p()
+    L = native.lib()
+    assert L.aqc_create(C.byref(h), 0, 0, 0, None, 0, None) == native.AQC_E_INVAL
+    assert L.aqc_create(C.byref(h), 0, 5, 10, None, 0, None) == native.AQC_E_INVAL
+    assert L.aqc_create(C.byref(h), 0, 0, 10, None, 0, None) == native.AQC_E_NOMEM
+    assert b"workspace" in L.aqc_last_error(None)
+    assert h.value is None
+    assert native.aqc_version().startswith("aqc-gb300")
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The package never imports the oracle (test infrastructure only)."""
+    root = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1311_3938_gb300")
+    for dp, _, fs in os.walk(root):
+        for f in fs:
+            if f.endswith((".py", ".cu", ".h", ".cuh", ".cpp")):
+                txt = open(os.path.join(dp, f)).read()
+                assert "oracle" not in txt.lower().replace("oracle_", ""), f
