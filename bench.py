@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Benchmark of the adiabatic-evolution hot path on one GB300 (or N replicas).
+
+Workload (one bench step = one pass of the whole hot path over one synthetic instance):
+  Exact-Cover-3 instance, n = 28 qubits, seed 3; linear path H = (1-s) H_i + s H_f,
+  s = t/T, T = 100; uniform start |S>; fixed-step grid from the step rule (kappa = 0.1).
+  Each step: set psi(0) -> 3 RK4 start-up steps -> PEC steps (one fused H*psi per step) up to
+  `--pec` grid steps -> P_1 and E(T-window) readback.  State in complex64 (headline) and
+  complex128 (reported beside it).
+Metric: H*psi GB/s = algorithmic bytes of the hot path / device time (inputs resident in HBM),
+with the fused PEC step's achieved bandwidth against the measured HBM copy peak.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_QUBITS = 28
+SEED = 3
+T_RUN = 100.0
+PEC_DEFAULT = 64
+METRIC = "H*psi GB/s (EC3 n=28 fused PEC step, algorithmic bytes)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--pec", type=int, default=PEC_DEFAULT, help="PEC steps per bench step")
+    ap.add_argument("--n", type=int, default=N_QUBITS)
+    ap.add_argument("--no-c128", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- accounting
+def alg_bytes(n, amp, pec_steps):
+    """Algorithmic bytes of one bench step: the minimum vector traffic of each operation.
+    PEC step 7 N b (read y, f_n, f_{n-1}, f_{n-2}, f_{n-3}; write y, f_{n+1}); RK4 step 18 N b;
+    f_3 + predictor 8 N b; init 1 N b; energy 1 N b."""
+    N = 1 << n
+    return N * amp * (7 * pec_steps + 18 * 3 + 8 + 1 + 1)
+
+
+def pec_flops_c128(n_flip, n_clause_classes=1):
+    """Algorithmic FP64 flops per amplitude of one PEC step: flip products 4 each (complex
+    amplitude times real coefficient, accumulated), diagonal 4 + 2 per clause class,
+    corrector and predictor 16 each, norm and error reductions 10."""
+    return 4 * n_flip + 4 + 2 * n_clause_classes + 32 + 10
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "api.cu", "aqc_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1311_3938_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(prec_name):
+    """dram bytes per PEC step from the committed ncu summary, if it was taken on the current
+    kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "pec_step_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(prec_name)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e.get("dram_bytes_per_pec_step")
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no-samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def cpu_sample(target_s=15.0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload: the same EC3
+    family / path / T at n = 22 (vectors far beyond CPU caches), first 3 RK4 + P PEC steps,
+    all host cores.  Returns (GB/s of algorithmic bytes, cores, description)."""
+    from instances import generate_ec3
+    from oracle import oracle as O
+
+    n = 22
+    inst = generate_ec3(n, SEED)
+    H = O.ec3_hamiltonian(inst)
+    sched = O.linear_path(T_RUN)
+    N = O.step_count(H, sched)
+    cores = os.cpu_count() or 1
+    psi0 = O.uniform_state(n)
+    t0 = time.perf_counter()
+    O.propagate(H, sched, N, psi0, max_steps=4, nthreads=cores)  # 3 RK4 + 1 PEC: 14 evaluations
+    t_probe = time.perf_counter() - t0
+    per_eval = t_probe / 14.0
+    pec = max(1, min(2000, int((target_s - t_probe) / max(per_eval, 1e-6))))
+    t0 = time.perf_counter()
+    O.propagate(H, sched, N, psi0, max_steps=3 + pec, nthreads=cores)
+    dt = time.perf_counter() - t0
+    gbs = alg_bytes(n, 16, pec) / dt / 1e9
+    desc = (f"FP64 oracle (plain C, {cores} threads) on the EC3 seed-{SEED} linear T={T_RUN:g} workload at n={n}: "
+            f"3 RK4 + {pec} PEC steps of its step grid, {dt:.1f} s")
+    return gbs, cores, desc, dt
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    import paper_1311_3938_gb300 as P
+    from instances import generate_ec3
+    from paper_1311_3938_gb300 import hamiltonians as HB
+    from paper_1311_3938_gb300.engine import Context
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    P.build()
+    n = a.n
+    inst = generate_ec3(n, SEED)
+    hbm_peak, peak_kind = peaks()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def measure(prec):
+        amp = 16 if prec == P.AQC_C128 else 8
+        ctx = Context(n, prec, device=local)
+        HB.load_ec3(ctx, inst)
+        ctx.set_schedule(T_RUN, HB.linear_schedule())
+        ctx.set_integrator(0, 0.0)
+        stream = ctx.stream
+        pec_ms = []
+        res = {}
+
+        def bench_step(record):
+            ctx.set_initial_state("uniform")
+            ctx.propagate(4, stats=False)  # 3 RK4 + f_3 + predictor + 1 PEC
+            st = ctx.propagate(a.pec - 1, stats=True)  # timed PEC steps (events on ctx stream)
+            if record:
+                pec_ms.append(st["elapsed_ms"] / (a.pec - 1))
+            res["P1"] = ctx.fidelity(inst.solution)
+            res["E"] = ctx.energy(P.AQC_GRP_B)
+            res["st"] = st
+
+        for _ in range(a.warmup):
+            bench_step(False)
+        barrier()
+        torch.cuda.synchronize()
+        clk = Clocks(local)
+        clk.start()
+        l0 = ctx.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            bench_step(True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = clk.stop()
+        launches = ctx.launch_count() - l0
+        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(ms)
+        ab = alg_bytes(n, amp, a.pec)
+        value = ab * a.steps * world / (ms * 1e-3) / 1e9
+        pec_step_ms = statistics.mean(pec_ms)
+        pec_ach = 7 * (1 << n) * amp / (pec_step_ms * 1e-3) / 1e9
+        out = {
+            "value": value,
+            "ms_per_step": ms / a.steps,
+            "pec_step_ms": pec_step_ms,
+            "pec_step_gbs": pec_ach,
+            "P1": res["P1"],
+            "E": res["E"],
+            "n_steps_grid": res["st"]["n_steps"],
+            "t_end": res["st"]["t"],
+            "launches": launches,
+            "clocks": clocks,
+        }
+        # end-to-end through the public API with host buffers
+        if not a.no_e2e:
+            host_in = torch.empty(1 << n, dtype=torch.complex64 if amp == 8 else torch.complex128).pin_memory()
+            host_in.fill_(1.0 / math.sqrt(1 << n))
+            host_out = torch.empty_like(host_in).pin_memory()
+
+            def e2e_step():
+                ctx.set_initial_state(host_in)  # H2D inside the call
+                ctx.propagate(a.pec + 3, stats=False)
+                ctx.fidelity(inst.solution)
+                ctx.energy(P.AQC_GRP_B)
+                ctx.state_into(host_out)  # D2H inside the call
+
+            e2e_step()
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(a.steps):
+                e2e_step()
+            torch.cuda.synchronize()
+            dt = max_over_ranks(time.perf_counter() - t0)
+            out["e2e"] = {
+                "value": ab * a.steps * world / dt / 1e9,
+                "unit": "GB/s",
+                "h2d_bytes_per_step": (1 << n) * amp,
+                "d2h_bytes_per_step": (1 << n) * amp + 16,
+            }
+            del host_in, host_out
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+        return out
+
+    r64 = measure(P.AQC_C64)
+    r128 = None if a.no_c128 else measure(P.AQC_C128)
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        gbs, cores, desc, _ = cpu_sample()
+        cpu = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc}
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    traffic = profiled_traffic("c64")
+    line = {
+        "metric": METRIC,
+        "value": r64["value"],
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": r64["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64 (f32 arithmetic, f64 reductions)",
+        "data": "synthetic (seeded EC3 instance)",
+        "config": {
+            "workload": f"ec3-n{n}-seed{SEED}-linear-T{T_RUN:g}-uniform",
+            "n_qubits": n,
+            "path": "linear s=t/T",
+            "T": T_RUN,
+            "grid_steps": r64["n_steps_grid"],
+            "bench_step": f"init + 3 RK4 + {a.pec} PEC grid steps + P1/E readback",
+            "parallelism": f"replicas x{world}",
+            "l2": f"no flush: each state vector ({(1 << n) * 8 / 2**30:.0f} GiB) is far larger than L2",
+        },
+        "roofline": {
+            "bound": "hbm",
+            "kernel": "fused PEC step (k_apply partial layouts + MODE_STEP), per grid step",
+            "achieved": r64["pec_step_gbs"],
+            "peak": hbm_peak,
+            "peak_kind": peak_kind,
+            "unit": "GB/s",
+            "frac": r64["pec_step_gbs"] / hbm_peak,
+            "traffic": traffic,
+            "alg_bytes_per_launch": 7 * (1 << n) * 8,
+        },
+        "cpu_baseline": cpu,
+        "e2e": r64.get("e2e"),
+        "gpu_launches": r64["launches"],
+        "clocks": r64["clocks"],
+        "fidelity_P1_window": r64["P1"],
+    }
+    if r128 is not None:
+        flops = pec_flops_c128(n) * (1 << n)
+        line["c128"] = {
+            "value": r128["value"],
+            "unit": "GB/s",
+            "ms_per_step": r128["ms_per_step"],
+            "pec_step_ms": r128["pec_step_ms"],
+            "roofline": {
+                "bound": "alu",
+                "achieved": flops / (r128["pec_step_ms"] * 1e-3) / 1e12,
+                "peak": 1.25,
+                "peak_kind": "nominal FP64 (profiling recipe)",
+                "unit": "TFLOP/s",
+                "frac": flops / (r128["pec_step_ms"] * 1e-3) / 1e12 / 1.25,
+                "hbm_frac": r128["pec_step_gbs"] / hbm_peak,
+                "traffic": profiled_traffic("c128"),
+            },
+            "e2e": r128.get("e2e"),
+            "gpu_launches": r128["launches"],
+            "clocks": r128["clocks"],
+            "P1_c128_minus_c64": r128["P1"] - r64["P1"],
+        }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(a):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = max(5.0, min(20.0, 150.0 / max(1, a.steps + a.warmup)))
+    for _ in range(a.warmup):
+        cpu_sample(per_step)
+    vals, secs, desc, cores = [], [], "", 1
+    for _ in range(a.steps):
+        gbs, cores, desc, dt = cpu_sample(per_step)
+        vals.append(gbs)
+        secs.append(dt)
+    v = statistics.mean(vals)
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": v,
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": 1e3 * statistics.mean(secs),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded EC3 instance)",
+        "config": {"workload": f"ec3-n{N_QUBITS}-seed{SEED}-linear-T{T_RUN:g}-uniform",
+                   "sample": "n=22 member of the same workload family, bounded step count"},
+        "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

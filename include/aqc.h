@@ -75,6 +75,7 @@ typedef struct {
   double max_err_est;  /* max over PEC steps of (19/270) ||y_{n+1} - p_{n+1}||           */
   double last_err_est; /* the same for the last PEC step                                 */
   double elapsed_ms;   /* device time of the call (CUDA events on the context stream)    */
+  int64_t launches;    /* kernel launches this call issued                               */
 } aqc_stats;
 
 /* ---- lifetime ---------------------------------------------------------------------- */
@@ -158,6 +159,9 @@ int aqc_norm2(aqc_ctx *ctx, double *out);
  * must not overlap a propagation of the same context (same stream ordering suffices).
  * This is the stand-alone SQH matvec of Sec. I.A. */
 int aqc_hpsi(aqc_ctx *ctx, double t, const void *psi, void *out);
+
+/* Total kernel launches the context has issued since creation (monotone counter). */
+int aqc_launch_count(const aqc_ctx *ctx, int64_t *out);
 
 /* Message of the last error of ctx (or of the last failed aqc_create if ctx is NULL). */
 const char *aqc_last_error(const aqc_ctx *ctx);

@@ -46,6 +46,7 @@ class aqc_stats(C.Structure):
         ("max_err_est", C.c_double),
         ("last_err_est", C.c_double),
         ("elapsed_ms", C.c_double),
+        ("launches", C.c_int64),
     ]
 
     def as_dict(self):
@@ -80,6 +81,7 @@ def lib():
             "aqc_energy": (i32, [vp, i32, C.POINTER(dbl)]),
             "aqc_norm2": (i32, [vp, C.POINTER(dbl)]),
             "aqc_hpsi": (i32, [vp, dbl, vp, vp]),
+            "aqc_launch_count": (i32, [vp, C.POINTER(i64)]),
             "aqc_last_error": (C.c_char_p, [vp]),
             "aqc_version": (C.c_char_p, []),
         }
@@ -181,6 +183,12 @@ def aqc_norm2(ctx):
 
 def aqc_hpsi(ctx, t, psi_ptr, out_ptr):
     _check(ctx, lib().aqc_hpsi(ctx, float(t), C.c_void_p(psi_ptr), C.c_void_p(out_ptr)))
+
+
+def aqc_launch_count(ctx):
+    out = C.c_int64()
+    _check(ctx, lib().aqc_launch_count(ctx, C.byref(out)))
+    return out.value
 
 
 def aqc_last_error(ctx):

@@ -43,12 +43,14 @@ std::vector<Layout> layouts_for(int n, int prec) {
     ls.push_back(Layout{n, n, 0, n});
     return ls;
   }
+  // every layout gets full-size tiles: the last one overlaps its predecessor if needed
   ls.push_back(Layout{tmax, tmax, 0, tmax});
+  const int w = tmax - cc;
   int start = tmax;
   while (start < n) {
-    const int w = std::min(tmax - cc, n - start);
-    ls.push_back(Layout{cc, start, w, cc + w});
-    start += w;
+    const int h = std::min(start, n - w);
+    ls.push_back(Layout{cc, h, w, cc + w});
+    start = h + w;
   }
   return ls;
 }
@@ -60,7 +62,7 @@ size_t max_tiles(int n, int prec) {
 }
 
 struct WsPlan {
-  size_t off_tab, off_slots, off_counter, off_partials, off_vec, vec_bytes, total;
+  size_t off_tab, off_slots, off_counter, off_partials, off_dcode, off_vec, vec_bytes, total;
   size_t partial_doubles;
 };
 
@@ -73,7 +75,8 @@ WsPlan plan_workspace(int n, int prec) {
   w.off_partials = w.off_counter + 256;
   size_t g = std::max(max_tiles(n, prec), (size_t)reduce_grid((uint64_t)1 << n));
   w.partial_doubles = 3 * g;
-  w.off_vec = align_up(w.off_partials + w.partial_doubles * sizeof(double), 256);
+  w.off_dcode = align_up(w.off_partials + w.partial_doubles * sizeof(double), 256);
+  w.off_vec = align_up(w.off_dcode + ((size_t)1 << n), 256);
   w.vec_bytes = align_up(((size_t)1 << n) * amp, 256);
   w.total = w.off_vec + V_COUNT * w.vec_bytes;
   return w;
@@ -95,14 +98,16 @@ struct aqc_ctx {
   double* d_slots = nullptr;
   unsigned* d_counter = nullptr;
   double* d_partials = nullptr;
+  uint8_t* d_dcode = nullptr;
   DevTables* h_tab = nullptr;
 
   std::vector<TermH> terms;
   std::vector<ClauseH> clauses;
   bool dirty = true;
   std::vector<Layout> layouts;
-  std::vector<int> nflips;  // local flips per layout
+  std::vector<int> nplain, ngeneral;  // local X-string / general products per layout
   int n_remote = 0, n_z = 0;
+  int table_class = -1;
 
   bool have_sched = false;
   int s_kind = 0;
@@ -115,6 +120,7 @@ struct aqc_ctx {
   bool hist_ready = false;
   int64_t step = 0, nsteps = 0, evals = 0;
   double h = 0;
+  int64_t launches = 0;  // kernel launches issued (monotone counter)
 
   std::string err;
 };
@@ -207,12 +213,26 @@ int build_tables(aqc_ctx* c) {
     per[where].push_back(f);
   }
   int pos = 0;
-  c->nflips.assign(nl, 0);
+  c->nplain.assign(nl, 0);
+  c->ngeneral.assign(nl, 0);
   for (int l = 0; l <= nl; l++) {
     t->flip_begin[l] = pos;
     if (pos + (int)per[l].size() > kMaxFlips) FAIL(c, AQC_E_UNSUPPORTED, "more than %d off-diagonal products", kMaxFlips);
-    for (const DevFlip& f : per[l]) t->flips[pos++] = f;
-    if (l < nl) c->nflips[l] = (int)per[l].size();
+    // X strings with real coefficients first (the kernel's fast loop), then general products
+    int np = 0;
+    if (l < nl) {
+      for (const DevFlip& f : per[l])
+        if (f.zm == 0) t->flips[pos + np++] = f;
+    }
+    int k = np;
+    for (const DevFlip& f : per[l])
+      if (l == nl || f.zm != 0) t->flips[pos + k++] = f;
+    t->plain_count[l] = np;
+    if (l < nl) {
+      c->nplain[l] = np;
+      c->ngeneral[l] = (int)per[l].size() - np;
+    }
+    pos += (int)per[l].size();
   }
   t->flip_begin[nl + 1] = pos;
   t->n_remote = (int)per[nl].size();
@@ -249,7 +269,19 @@ int build_tables(aqc_ctx* c) {
     t->classes[k] = classes[k];
   }
   t->n_classes = (int)classes.size();
+  // cache the counts of clause class 0 as one byte per index when they fit
+  t->table_class = -1;
+  if (!classes.empty()) {
+    const int cnt = classes[0].end - classes[0].begin;
+    const int maxv = classes[0].pen == AQC_PEN_SQUARED ? 4 * cnt : cnt;
+    if (maxv <= 255) t->table_class = 0;
+  }
+  c->table_class = t->table_class;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_tab, t, sizeof(DevTables), cudaMemcpyHostToDevice, c->stream));
+  if (t->table_class >= 0) {
+    CUDA_TRY(c, launch_diag_codes(c->d_dcode, c->N, c->d_tab, t->table_class, c->stream));
+    c->launches++;
+  }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->dirty = false;
   return AQC_OK;
@@ -298,28 +330,36 @@ ApplyParams base_params(aqc_ctx* c) {
   return p;
 }
 
-// One evaluation of H(t) src over all layouts; the last layout runs the mode epilogue.
+// One evaluation of H(t) src over all layouts.  The strided layouts run first as partial sums
+// (the first one also adds the diagonal and the products no layout holds); the contiguous
+// layout 0 runs last with the mode epilogue, so the kernel touching the most vectors has the
+// smallest page footprint per tile.
 int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, void* partial_out) {
   const int nl = (int)c->layouts.size();
-  for (int l = 0; l < nl; l++) {
-    ApplyParams p = (l == nl - 1) ? fin : base_params(c);
+  for (int step = 0; step < nl; step++) {
+    const int l = nl - 1 - step;
+    const bool first = (step == 0), last = (l == 0);
+    ApplyParams p = last ? fin : base_params(c);
     p.L = c->layouts[l];
     p.layout_index = l;
-    p.with_diag = (l == 0);
-    p.with_remote = (l == 0);
+    p.with_diag = first;
+    p.with_remote = first;
     for (int g = 0; g < 3; g++) p.w[g] = w[g];
     p.src = src;
-    p.qin = (l == 0) ? nullptr : c->vec[V_Q];
-    if (l < nl - 1) {
+    p.qin = first ? nullptr : c->vec[V_Q];
+    if (!last) {
       p.mode = MODE_PARTIAL;
       p.qout = c->vec[V_Q];
     } else if (fin.mode == MODE_PARTIAL) {
       p.qout = partial_out;
     }
-    const int grid = 1 << (c->n - p.L.t);
-    const size_t smem = apply_smem_bytes(c->prec, p.L.t, c->nflips[l], l == 0 ? c->n_remote : 0, l == 0 ? c->n_z : 0);
+    p.dcode = (first && c->table_class >= 0) ? c->d_dcode : nullptr;
+    p.ntiles = 1u << (c->n - p.L.t);
+    const size_t smem = apply_smem_bytes(c->prec, p.L.t, c->nplain[l], c->ngeneral[l] + (first ? c->n_remote : 0),
+                                         first ? c->n_z : 0);
     if (smem > 227 * 1024) FAIL(c, AQC_E_UNSUPPORTED, "shared memory %zu bytes too large", smem);
-    CUDA_TRY(c, launch_apply(c->prec, p, grid, (int)smem, c->stream));
+    CUDA_TRY(c, launch_apply(c->prec, p, (int)smem, c->stream));
+    c->launches++;
   }
   return AQC_OK;
 }
@@ -367,6 +407,7 @@ int start_history(aqc_ctx* c) {
   c->evals++;
   CUDA_TRY(c, launch_predict(c->prec, c->vec[V_P], c->vec[V_Y], c->vec[V_F0 + 3], c->vec[V_F0 + 2],
                              c->vec[V_F0 + 1], c->vec[V_F0 + 0], c->h, c->N, c->stream));
+  c->launches++;
   c->hist_ready = true;
   return AQC_OK;
 }
@@ -455,6 +496,7 @@ int aqc_create(aqc_ctx** out, int device, int precision, int n_qubits, void* wor
   c->d_slots = (double*)(c->ws + wp.off_slots);
   c->d_counter = (unsigned*)(c->ws + wp.off_counter);
   c->d_partials = (double*)(c->ws + wp.off_partials);
+  c->d_dcode = (uint8_t*)(c->ws + wp.off_dcode);
   for (int v = 0; v < V_COUNT; v++) c->vec[v] = c->ws + wp.off_vec + (size_t)v * wp.vec_bytes;
   for (int g = 0; g < 3; g++)
     for (int k = 0; k < 4; k++) c->poly[g][k] = 0.0;
@@ -561,10 +603,12 @@ int aqc_set_initial_state(aqc_ctx* ctx, int kind, uint64_t basis, const void* us
   switch (kind) {
     case AQC_INIT_UNIFORM:
       CUDA_TRY(ctx, launch_init(ctx->prec, y, ctx->N, 0, 0, ctx->stream));
+      ctx->launches++;
       break;
     case AQC_INIT_BASIS:
       if (basis >= ctx->N) FAIL(ctx, AQC_E_INVAL, "basis index >= 2^n");
       CUDA_TRY(ctx, launch_init(ctx->prec, y, ctx->N, 1, basis, ctx->stream));
+      ctx->launches++;
       break;
     case AQC_INIT_USER_HOST:
       if (!user) FAIL(ctx, AQC_E_INVAL, "user vector is NULL");
@@ -597,6 +641,7 @@ int aqc_propagate(aqc_ctx* ctx, int64_t max_steps, aqc_stats* stats) {
     ctx->h = ctx->T / (double)ctx->nsteps;
   }
   const int64_t target = max_steps < 0 ? ctx->nsteps : std::min(ctx->nsteps, ctx->step + max_steps);
+  const int64_t launches0 = ctx->launches;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (stats) {
     CUDA_TRY(ctx, cudaEventCreate(&e0));
@@ -624,8 +669,10 @@ int aqc_propagate(aqc_ctx* ctx, int64_t max_steps, aqc_stats* stats) {
       stats->evaluations = ctx->evals;
       stats->h = ctx->h;
       stats->t = (double)ctx->step * ctx->h;
+      stats->launches = ctx->launches - launches0;
       cudaError_t e = launch_reduce(ctx->prec, 0, ctx->vec[V_Y], ctx->N, ctx->d_partials, ctx->d_counter,
                                     ctx->d_slots, reduce_grid(ctx->N), ctx->stream);
+      ctx->launches++;
       double sl[kSlotCount];
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(sl, ctx->d_slots, sizeof(sl), cudaMemcpyDeviceToHost, ctx->stream);
@@ -667,6 +714,7 @@ int aqc_fidelity(aqc_ctx* ctx, uint64_t w, double* out) {
   if (w >= ctx->N) FAIL(ctx, AQC_E_INVAL, "w >= 2^n");
   DeviceGuard dg(ctx->device);
   CUDA_TRY(ctx, launch_fidelity(ctx->prec, ctx->vec[V_Y], w, ctx->d_slots, ctx->stream));
+  ctx->launches++;
   return read_slot(ctx, kSlotDot, out);
 }
 
@@ -692,6 +740,7 @@ int aqc_norm2(aqc_ctx* ctx, double* out) {
   DeviceGuard dg(ctx->device);
   CUDA_TRY(ctx, launch_reduce(ctx->prec, 0, ctx->vec[V_Y], ctx->N, ctx->d_partials, ctx->d_counter, ctx->d_slots,
                               reduce_grid(ctx->N), ctx->stream));
+  ctx->launches++;
   return read_slot(ctx, kSlotNorm2, out);
 }
 
@@ -709,6 +758,12 @@ int aqc_hpsi(aqc_ctx* ctx, double t, const void* psi, void* out) {
   ApplyParams fin = base_params(ctx);
   fin.mode = MODE_PARTIAL;
   return evaluate(ctx, w, psi, fin, out);
+}
+
+int aqc_launch_count(const aqc_ctx* ctx, int64_t* out) {
+  if (!ctx || !out) return AQC_E_INVAL;
+  *out = ctx->launches;
+  return AQC_OK;
 }
 
 const char* aqc_last_error(const aqc_ctx* ctx) {

@@ -45,9 +45,11 @@ struct DevTables {
   int n_layouts;
   int n_remote;                     // flips no layout holds, gathered from global memory
   int flip_begin[kMaxLayouts + 2];  // layout l: [flip_begin[l], flip_begin[l+1]); remote after
+  int plain_count[kMaxLayouts + 2]; // leading X-string products (zm = 0, real) of each range
   int n_z;
   int n_classes;
-  int pad[2];
+  int table_class;                  // clause class whose counts are in the per-index byte table, or -1
+  int pad;
   double ident[3];                  // identity prefactors per group (energy shifts m^(0))
   DevClass classes[kMaxClasses];
   uint32_t clause_mask[kMaxClauses];
@@ -66,6 +68,7 @@ enum Mode : int {
 struct ApplyParams {
   const DevTables* tab;
   int n;
+  uint32_t ntiles;   // 2^(n - L.t); CTAs loop over tiles blockIdx.x, blockIdx.x + gridDim.x, ...
   Layout L;
   int layout_index;
   int with_diag;
@@ -74,6 +77,7 @@ struct ApplyParams {
   int stage;         // RK4 stage 1..4
   double w[3];       // group weights A, B, C at the evaluation time
   double h;
+  const uint8_t* dcode; // per-index clause counts of class table_class (nullable)
   const void* src;   // vector the Hamiltonian acts on
   const void* qin;   // partial sum from earlier layouts (nullable)
   void* qout;        // PARTIAL: output partial sum
@@ -97,8 +101,10 @@ constexpr int kSlotDot = 3;
 constexpr int kSlotDotIm = 4;
 constexpr int kSlotCount = 8;
 
-cudaError_t launch_apply(int prec, const ApplyParams& p, int grid, int smem_bytes, cudaStream_t s);
-size_t apply_smem_bytes(int prec, int t, int n_local_flips, int n_remote, int n_z);
+cudaError_t launch_apply(int prec, const ApplyParams& p, int smem_bytes, cudaStream_t s);
+int apply_grid(int prec, int mode, uint32_t ntiles, int smem_bytes);
+size_t apply_smem_bytes(int prec, int t, int n_plain, int n_general, int n_z);
+cudaError_t launch_diag_codes(uint8_t* out, uint64_t N, const DevTables* tab, int cls, cudaStream_t s);
 cudaError_t launch_init(int prec, void* y, uint64_t N, int kind, uint64_t basis, cudaStream_t s);
 cudaError_t launch_predict(int prec, void* p, const void* y, const void* f3, const void* f2, const void* f1,
                            const void* f0, double h, uint64_t N, cudaStream_t s);

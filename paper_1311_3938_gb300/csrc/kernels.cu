@@ -4,10 +4,13 @@
 //    2^n index space spanned by the layout's tile bits [0,c) and [h,h+w) (Layout); the CTA
 //    stages the source vector's tile in shared memory, so every Pauli product whose flip
 //    mask lies inside the tile bits is a shared-memory gather (Sec. I.A: each product maps
-//    |z> to one basis state z^x with a phase).  Diagonal parts (Z strings, clause penalties
-//    of Eq. hci / Eq. sat) are computed from the index, never stored.  Products no layout
-//    holds ("remote") are gathered from global memory.  The epilogue depends on MODE:
-//    partial sum, fused PEC step (Sec. I.B), Runge-Kutta stage, derivative, or energy.
+//    |z> to one basis state z^x with a phase).  Each thread keeps kV points in registers and
+//    runs the term loop outside the point loop, so a term's mask and coefficient are read
+//    once per kV points.  Diagonal parts (Z strings, clause penalties of Eq. hci / Eq. sat)
+//    come from the index; the clause counts of one clause class are cached as one byte per
+//    index (k_diag_codes, computed once per Hamiltonian).  Products no layout holds
+//    ("remote") are gathered from global memory.  The epilogue depends on MODE: partial sum,
+//    fused PEC step (Sec. I.B), Runge-Kutta stage, derivative, or energy.
 //  Reductions accumulate in FP64 per thread -> warp -> CTA -> last-CTA sum in fixed order,
 //  so results are bitwise reproducible.
 #include <cuda_runtime.h>
@@ -35,11 +38,42 @@ struct SFlip {
   R cr, ci;                  // effective coefficient coef * w_group * i^ipow
 };
 
+// X-string product with a real coefficient: the hot case (driver and XX terms)
+template <typename R>
+struct PFlip;
+template <>
+struct PFlip<float> {
+  uint32_t lx;
+  float c;
+};
+template <>
+struct PFlip<double> {
+  uint32_t lx;
+  uint32_t pad;
+  double c;
+};
+
 template <typename R>
 struct SZ {
   uint32_t zm;
   uint32_t pad;
   R c;
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+// dynamic shared memory map of k_apply: [tile][plain flips][general flips][Z strings][reduction]
+template <typename R>
+struct SmemMap {
+  size_t pf, gf, zs, red, total;
+  __host__ __device__ SmemMap(uint32_t tsize, int np, int ng, int nz) {
+    using C2 = typename Cplx<R>::T;
+    pf = align16((size_t)tsize * sizeof(C2));
+    gf = align16(pf + (size_t)np * sizeof(PFlip<R>));
+    zs = align16(gf + (size_t)ng * sizeof(SFlip<R>));
+    red = align16(zs + (size_t)nz * sizeof(SZ<R>));
+    total = red + 8 * 2 * sizeof(double) + 16;
+  }
 };
 
 __device__ __forceinline__ uint32_t tile_base(const Layout& L, uint32_t b) {
@@ -80,20 +114,20 @@ __device__ __forceinline__ void cta_reduce(double (&v)[K], double* s_red) {
 }
 
 // Per-CTA partials -> last CTA sums them in CTA order.  Returns true in thread 0 of the last
-// CTA, with the totals in v.
+// CTA, with the totals in v.  s_red holds >= 8*K doubles plus one int flag after them.
 template <int K>
 __device__ bool grid_reduce(double (&v)[K], double* partials, unsigned* counter, double* s_red) {
-  __shared__ bool s_last;
+  int* s_last = reinterpret_cast<int*>(s_red + 8 * K);
   cta_reduce<K>(v, s_red);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < K; k++) partials[(size_t)blockIdx.x * K + k] = v[k];
     __threadfence();
     unsigned ticket = atomicAdd(counter, 1u);
-    s_last = (ticket == gridDim.x - 1);
+    *s_last = (ticket == gridDim.x - 1) ? 1 : 0;
   }
   __syncthreads();
-  if (!s_last) return false;
+  if (!*s_last) return false;
   __threadfence();
   double a[K];
 #pragma unroll
@@ -112,28 +146,68 @@ __device__ bool grid_reduce(double (&v)[K], double* partials, unsigned* counter,
   return false;
 }
 
+template <typename R>
+__device__ __forceinline__ R clause_count(const DevTables* __restrict__ tab, const DevClass& cl, uint32_t z) {
+  int cnt = 0;
+  if (cl.pen == 0) {
+    for (int k = cl.begin; k < cl.end; k++) cnt += (__popc(tab->clause_mask[k] & z) != 1);
+  } else {
+    for (int k = cl.begin; k < cl.end; k++) {
+      const int o = 1 - __popc(tab->clause_mask[k] & z);
+      cnt += o * o;
+    }
+  }
+  return (R)cnt;
+}
+
+constexpr int kThreads = 256;
+constexpr int kVf = 4;  // points per thread held in registers while the term loop runs (FP32)
+constexpr int kVd = 2;  // the same for FP64 (the FP64 pipe, not memory, bounds that path)
+
+// 16-byte global -> shared copies that do not pass through registers (many in flight per thread)
+__device__ __forceinline__ void cp_async16(void* smem_ptr, const void* gptr) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_ptr);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gptr) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <typename R, int MODE>
-__global__ void __launch_bounds__(256) k_apply(const ApplyParams P) {
+__global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
   using C2 = typename Cplx<R>::T;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double s_red[8 * 3];
 
   const Layout L = P.L;
   const uint32_t tsize = 1u << L.t;
-  const DevTables* tab = P.tab;
-  const int fb = tab->flip_begin[P.layout_index];
-  const int nloc = tab->flip_begin[P.layout_index + 1] - fb;
+  const uint32_t tmask = tsize - 1u;
+  const DevTables* __restrict__ tab = P.tab;
+  const int li = P.layout_index;
+  const int fb = tab->flip_begin[li];
+  const int np = tab->plain_count[li];
+  const int ngl = tab->flip_begin[li + 1] - fb - np;
   const int rb = tab->flip_begin[tab->n_layouts];
   const int nrem = P.with_remote ? tab->n_remote : 0;
+  const int ng = ngl + nrem;
   const int nz = P.with_diag ? tab->n_z : 0;
+  const SmemMap<R> map(tsize, np, ng, nz);
 
   C2* s_p = reinterpret_cast<C2*>(smem);
-  SFlip<R>* s_f = reinterpret_cast<SFlip<R>*>(smem + (size_t)tsize * sizeof(C2));
-  SZ<R>* s_z = reinterpret_cast<SZ<R>*>(s_f + nloc + nrem);
+  PFlip<R>* s_pf = reinterpret_cast<PFlip<R>*>(smem + map.pf);
+  SFlip<R>* s_gf = reinterpret_cast<SFlip<R>*>(smem + map.gf);
+  SZ<R>* s_z = reinterpret_cast<SZ<R>*>(smem + map.zs);
+  double* s_red = reinterpret_cast<double*>(smem + map.red);
 
-  // effective coefficients for this evaluation time
-  for (int k = threadIdx.x; k < nloc + nrem; k += blockDim.x) {
-    const DevFlip d = tab->flips[k < nloc ? fb + k : rb + (k - nloc)];
+  // effective coefficients at this evaluation time
+  for (int k = threadIdx.x; k < np; k += blockDim.x) {
+    const DevFlip d = tab->flips[fb + k];
+    PFlip<R> f;
+    f.lx = d.lx;
+    f.c = (R)(d.coef * P.w[d.group]);
+    s_pf[k] = f;
+  }
+  for (int k = threadIdx.x; k < ng; k += blockDim.x) {
+    const DevFlip d = tab->flips[k < ngl ? fb + np + k : rb + (k - ngl)];
     const double c = d.coef * P.w[d.group];
     double cr = 0.0, ci = 0.0;
     switch (d.ipow & 3) {
@@ -143,13 +217,13 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams P) {
       default: ci = -c; break;
     }
     SFlip<R> f;
-    f.lx = d.lx;
+    f.lx = k < ngl ? d.lx : 0u;
     f.x = d.x;
     f.zm = d.zm;
     f.cplx = (d.ipow & 1);
     f.cr = (R)cr;
     f.ci = (R)ci;
-    s_f[k] = f;
+    s_gf[k] = f;
   }
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
     SZ<R> e;
@@ -158,124 +232,185 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams P) {
     e.c = (R)(tab->z[k].coef * P.w[tab->z[k].group]);
     s_z[k] = e;
   }
-  R dconst = (R)0;
-  if (P.with_diag) dconst = (R)(tab->ident[0] * P.w[0] + tab->ident[1] * P.w[1] + tab->ident[2] * P.w[2]);
-  const int ncls = P.with_diag ? tab->n_classes : 0;
+  R dconst = (R)0, wtab = (R)0;
+  int tcls = -1, ncls = 0;
+  if (P.with_diag) {
+    dconst = (R)(tab->ident[0] * P.w[0] + tab->ident[1] * P.w[1] + tab->ident[2] * P.w[2]);
+    ncls = tab->n_classes;
+    if (P.dcode) {
+      tcls = tab->table_class;
+      wtab = (R)(tab->classes[tcls].scale * P.w[tab->classes[tcls].group]);
+    }
+  }
 
-  const uint32_t zb = tile_base(L, blockIdx.x);
   const C2* __restrict__ src = reinterpret_cast<const C2*>(P.src);
-  for (uint32_t j = threadIdx.x; j < tsize; j += blockDim.x) s_p[j] = src[tile_z(L, j, zb)];
-  __syncthreads();
-
   double red[2] = {0.0, 0.0};
   const R h = (R)P.h;
-  for (uint32_t j = threadIdx.x; j < tsize; j += blockDim.x) {
-    const uint32_t z = tile_z(L, j, zb);
-    const C2 pv = s_p[j];
-    R ar = (R)0, ai = (R)0;
-    if (P.qin) {
-      const C2 q = reinterpret_cast<const C2*>(P.qin)[z];
-      ar = q.x;
-      ai = q.y;
+  constexpr bool kNeedY = (MODE == MODE_STEP || MODE == MODE_RK4);
+  constexpr bool kNeedF = (MODE == MODE_STEP);
+  const C2 zero2 = C2{(R)0, (R)0};
+  constexpr int kV = sizeof(R) == 4 ? kVf : kVd;
+  // persistent CTAs: one prologue and one reduction per CTA, tiles taken round-robin
+  for (uint32_t tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
+  // stage the source tile with asynchronous 16-byte copies: a pair of consecutive indices for
+  // complex64 (tile bit 0 is global bit 0), one index for complex128
+  __syncthreads();  // readers of the previous tile are done
+  const uint32_t zb = tile_base(L, tile);
+  {
+    constexpr uint32_t per16 = 16 / sizeof(C2);  // indices per 16-byte granule
+    const uint32_t granules = tsize / per16;
+    for (uint32_t g = threadIdx.x; g < granules; g += blockDim.x) {
+      const uint32_t j = g * per16;
+      cp_async16(s_p + j, src + tile_z(L, j, zb));
     }
-    if (P.with_diag) {
-      R d = dconst;
-      for (int k = 0; k < nz; k++) {
-        const SZ<R> e = s_z[k];
-        d += (__popc(e.zm & z) & 1) ? -e.c : e.c;
-      }
-      for (int c = 0; c < ncls; c++) {
-        const DevClass cl = tab->classes[c];
-        int cnt = 0;
-        if (cl.pen == 0) {
-          for (int k = cl.begin; k < cl.end; k++) cnt += (__popc(tab->clause_mask[k] & z) != 1);
-        } else {
-          for (int k = cl.begin; k < cl.end; k++) {
-            const int o = 1 - __popc(tab->clause_mask[k] & z);
-            cnt += o * o;
-          }
-        }
-        d += (R)(cl.scale * P.w[cl.group]) * (R)cnt;
-      }
-      ar += d * pv.x;
-      ai += d * pv.y;
-    }
-    for (int k = 0; k < nloc + nrem; k++) {
-      const SFlip<R> f = s_f[k];
-      C2 v;
-      if (k < nloc) {
-        v = s_p[j ^ f.lx];
-      } else {
-        v = src[z ^ f.x];
-      }
-      R cr = f.cr, ci = f.ci;
-      if (f.zm && (__popc(f.zm & (z ^ f.x)) & 1)) {
-        cr = -cr;
-        ci = -ci;
-      }
-      if (f.cplx) {
-        ar += cr * v.x - ci * v.y;
-        ai += cr * v.y + ci * v.x;
-      } else {
-        ar += cr * v.x;
-        ai += cr * v.y;
-      }
-    }
+    cp_async_wait_all();
+  }
+  __syncthreads();
 
-    if (MODE == MODE_PARTIAL) {
-      reinterpret_cast<C2*>(P.qout)[z] = C2{ar, ai};
-    } else if (MODE == MODE_DERIV) {
-      reinterpret_cast<C2*>(P.fout)[z] = C2{ai, -ar};  // -i (ar + i ai)
-    } else if (MODE == MODE_ENERGY) {
-      red[0] += (double)pv.x * (double)ar + (double)pv.y * (double)ai;
-      red[1] += (double)pv.x * (double)ai - (double)pv.y * (double)ar;
-    } else if (MODE == MODE_STEP) {
-      // f_{n+1} = -i H p_{n+1};  corrector y_{n+1};  predictor p_{n+2}  (Sec. I.B)
-      const C2 fn = C2{ai, -ar};
-      C2* yv = reinterpret_cast<C2*>(P.y);
-      const C2 y0 = yv[z];
-      const C2 a = reinterpret_cast<const C2*>(P.f0)[z];
-      const C2 b = reinterpret_cast<const C2*>(P.f1)[z];
-      const C2 c = reinterpret_cast<const C2*>(P.f2)[z];
-      const R h24 = h / (R)24;
-      C2 yn, pn;
-      yn.x = y0.x + h24 * ((R)9 * fn.x + (R)19 * a.x - (R)5 * b.x + c.x);
-      yn.y = y0.y + h24 * ((R)9 * fn.y + (R)19 * a.y - (R)5 * b.y + c.y);
-      pn.x = yn.x + h24 * ((R)55 * fn.x - (R)59 * a.x + (R)37 * b.x - (R)9 * c.x);
-      pn.y = yn.y + h24 * ((R)55 * fn.y - (R)59 * a.y + (R)37 * b.y - (R)9 * c.y);
-      yv[z] = yn;
-      reinterpret_cast<C2*>(P.fout)[z] = fn;
-      reinterpret_cast<C2*>(P.pout)[z] = pn;
-      const double dx = (double)yn.x - (double)pv.x, dy = (double)yn.y - (double)pv.y;
-      red[0] += (double)yn.x * (double)yn.x + (double)yn.y * (double)yn.y;
-      red[1] += dx * dx + dy * dy;
-    } else if (MODE == MODE_RK4) {
-      const C2 k = C2{ai, -ar};
-      C2* yv = reinterpret_cast<C2*>(P.y);
-      C2* acc = reinterpret_cast<C2*>(P.acc);
-      C2* ys = reinterpret_cast<C2*>(P.pout);
-      const C2 y0 = yv[z];
-      if (P.stage == 1) {
-        reinterpret_cast<C2*>(P.fout)[z] = k;
-        acc[z] = k;
-        const R hh = (R)0.5 * h;
-        ys[z] = C2{y0.x + hh * k.x, y0.y + hh * k.y};
-      } else if (P.stage == 2 || P.stage == 3) {
-        C2 a = acc[z];
-        a.x += (R)2 * k.x;
-        a.y += (R)2 * k.y;
-        acc[z] = a;
-        const R hh = P.stage == 2 ? (R)0.5 * h : h;
-        ys[z] = C2{y0.x + hh * k.x, y0.y + hh * k.y};
-      } else {
-        C2 a = acc[z];
-        a.x += k.x;
-        a.y += k.y;
-        const R h6 = h / (R)6;
-        yv[z] = C2{y0.x + h6 * a.x, y0.y + h6 * a.y};
+  // reductions: per-thread partials over one tile in the state precision (a few dozen
+  // points), promoted to FP64 once per tile; FP64 across tiles, CTAs and the grid
+  R rt0 = (R)0, rt1 = (R)0;
+  for (uint32_t base = threadIdx.x; base < tsize; base += blockDim.x * kV) {
+    uint32_t jm[kV], z[kV];
+    bool ok[kV];
+#pragma unroll
+    for (int v = 0; v < kV; v++) {
+      const uint32_t j = base + (uint32_t)v * blockDim.x;
+      ok[v] = j < tsize;
+      jm[v] = j & tmask;
+      z[v] = tile_z(L, jm[v], zb);
+    }
+    // 1. issue this chunk's pointwise global loads first; they complete while the
+    //    shared-memory gathers below run
+    C2 qv[kV], y0[kV], a[kV], b[kV], c[kV];
+    uint32_t code[kV];
+#pragma unroll
+    for (int v = 0; v < kV; v++) {
+      qv[v] = (P.qin && ok[v]) ? reinterpret_cast<const C2*>(P.qin)[z[v]] : zero2;
+      code[v] = (tcls >= 0 && ok[v]) ? (uint32_t)P.dcode[z[v]] : 0u;
+      if (kNeedY) y0[v] = ok[v] ? reinterpret_cast<const C2*>(P.y)[z[v]] : zero2;
+      if (kNeedF) {
+        a[v] = ok[v] ? reinterpret_cast<const C2*>(P.f0)[z[v]] : zero2;
+        b[v] = ok[v] ? reinterpret_cast<const C2*>(P.f1)[z[v]] : zero2;
+        c[v] = ok[v] ? reinterpret_cast<const C2*>(P.f2)[z[v]] : zero2;
+      } else if (MODE == MODE_RK4) {
+        a[v] = (ok[v] && P.stage > 1) ? reinterpret_cast<const C2*>(P.acc)[z[v]] : zero2;
+      }
+    }
+    // 2. X strings with real coefficients: shared-memory gathers
+    R ar[kV], ai[kV];
+#pragma unroll
+    for (int v = 0; v < kV; v++) {
+      ar[v] = (R)0;
+      ai[v] = (R)0;
+    }
+    for (int k = 0; k < np; k++) {
+      const PFlip<R> f = s_pf[k];
+#pragma unroll
+      for (int v = 0; v < kV; v++) {
+        const C2 u = s_p[jm[v] ^ f.lx];
+        ar[v] += f.c * u.x;
+        ai[v] += f.c * u.y;
+      }
+    }
+    // 3. general products (Y/Z phases, complex coefficients) and remote products
+    for (int k = 0; k < ng; k++) {
+      const SFlip<R> f = s_gf[k];
+#pragma unroll
+      for (int v = 0; v < kV; v++) {
+        C2 u;
+        if (k < ngl)
+          u = s_p[jm[v] ^ f.lx];
+        else
+          u = ok[v] ? src[z[v] ^ f.x] : zero2;
+        R cr = f.cr, ci = f.ci;
+        if (__popc(f.zm & (z[v] ^ f.x)) & 1) {
+          cr = -cr;
+          ci = -ci;
+        }
+        ar[v] += cr * u.x - ci * u.y;
+        ai[v] += cr * u.y + ci * u.x;
+      }
+    }
+    // 4. diagonal and partial sum of the earlier layouts
+#pragma unroll
+    for (int v = 0; v < kV; v++) {
+      if (P.with_diag) {
+        R d = dconst;
+        if (tcls >= 0) d += wtab * (R)code[v];
+        for (int cc = 0; cc < ncls; cc++) {
+          if (cc == tcls) continue;
+          const DevClass cl = tab->classes[cc];
+          d += (R)(cl.scale * P.w[cl.group]) * clause_count<R>(tab, cl, z[v]);
+        }
+        for (int k = 0; k < nz; k++) {
+          const SZ<R> e = s_z[k];
+          d += (__popc(e.zm & z[v]) & 1) ? -e.c : e.c;
+        }
+        const C2 pv = s_p[jm[v]];
+        ar[v] += d * pv.x;
+        ai[v] += d * pv.y;
+      }
+      ar[v] += qv[v].x;
+      ai[v] += qv[v].y;
+    }
+    // 5. epilogue
+    const R h24 = h / (R)24;
+#pragma unroll
+    for (int v = 0; v < kV; v++) {
+      if (!ok[v]) continue;
+      const uint32_t zz = z[v];
+      if (MODE == MODE_PARTIAL) {
+        reinterpret_cast<C2*>(P.qout)[zz] = C2{ar[v], ai[v]};
+      } else if (MODE == MODE_DERIV) {
+        reinterpret_cast<C2*>(P.fout)[zz] = C2{ai[v], -ar[v]};  // -i (ar + i ai)
+      } else if (MODE == MODE_ENERGY) {
+        const C2 pv = s_p[jm[v]];
+        rt0 += pv.x * ar[v] + pv.y * ai[v];
+        rt1 += pv.x * ai[v] - pv.y * ar[v];
+      } else if (MODE == MODE_STEP) {
+        // f_{n+1} = -i H p_{n+1};  corrector y_{n+1};  predictor p_{n+2}  (Sec. I.B)
+        const C2 fn = C2{ai[v], -ar[v]};
+        C2 yn, pn;
+        yn.x = y0[v].x + h24 * ((R)9 * fn.x + (R)19 * a[v].x - (R)5 * b[v].x + c[v].x);
+        yn.y = y0[v].y + h24 * ((R)9 * fn.y + (R)19 * a[v].y - (R)5 * b[v].y + c[v].y);
+        pn.x = yn.x + h24 * ((R)55 * fn.x - (R)59 * a[v].x + (R)37 * b[v].x - (R)9 * c[v].x);
+        pn.y = yn.y + h24 * ((R)55 * fn.y - (R)59 * a[v].y + (R)37 * b[v].y - (R)9 * c[v].y);
+        reinterpret_cast<C2*>(P.y)[zz] = yn;
+        reinterpret_cast<C2*>(P.fout)[zz] = fn;
+        reinterpret_cast<C2*>(P.pout)[zz] = pn;
+        const C2 pv = s_p[jm[v]];
+        const R dx = yn.x - pv.x, dy = yn.y - pv.y;
+        rt0 += yn.x * yn.x + yn.y * yn.y;
+        rt1 += dx * dx + dy * dy;
+      } else if (MODE == MODE_RK4) {
+        const C2 k = C2{ai[v], -ar[v]};
+        if (P.stage == 1) {
+          reinterpret_cast<C2*>(P.fout)[zz] = k;
+          reinterpret_cast<C2*>(P.acc)[zz] = k;
+          const R hh = (R)0.5 * h;
+          reinterpret_cast<C2*>(P.pout)[zz] = C2{y0[v].x + hh * k.x, y0[v].y + hh * k.y};
+        } else if (P.stage == 2 || P.stage == 3) {
+          C2 s2 = a[v];
+          s2.x += (R)2 * k.x;
+          s2.y += (R)2 * k.y;
+          reinterpret_cast<C2*>(P.acc)[zz] = s2;
+          const R hh = P.stage == 2 ? (R)0.5 * h : h;
+          reinterpret_cast<C2*>(P.pout)[zz] = C2{y0[v].x + hh * k.x, y0[v].y + hh * k.y};
+        } else {
+          C2 s2 = a[v];
+          s2.x += k.x;
+          s2.y += k.y;
+          const R h6 = h / (R)6;
+          reinterpret_cast<C2*>(P.y)[zz] = C2{y0[v].x + h6 * s2.x, y0[v].y + h6 * s2.y};
+        }
       }
     }
   }
+
+    red[0] += (double)rt0;
+    red[1] += (double)rt1;
+  }  // tile loop
 
   if (MODE == MODE_STEP || MODE == MODE_ENERGY) {
     if (grid_reduce<2>(red, P.partials, P.counter, s_red)) {
@@ -292,39 +427,78 @@ __global__ void __launch_bounds__(256) k_apply(const ApplyParams P) {
   }
 }
 
-size_t apply_smem_bytes(int prec, int t, int n_local_flips, int n_remote, int n_z) {
-  const size_t amp = prec == 0 ? 16 : 8;
-  const size_t fl = prec == 0 ? sizeof(SFlip<double>) : sizeof(SFlip<float>);
-  const size_t zz = prec == 0 ? sizeof(SZ<double>) : sizeof(SZ<float>);
-  return ((size_t)1 << t) * amp + (size_t)(n_local_flips + n_remote) * fl + (size_t)n_z * zz + 16;
+size_t apply_smem_bytes(int prec, int t, int n_plain, int n_general, int n_z) {
+  const uint32_t tsize = 1u << t;
+  return prec == 0 ? SmemMap<double>(tsize, n_plain, n_general, n_z).total
+                   : SmemMap<float>(tsize, n_plain, n_general, n_z).total;
 }
 
+// Persistent grid: (resident CTAs per SM for this smem size) x SMs, at most one CTA per tile.
 template <typename R, int MODE>
-static cudaError_t launch_one(const ApplyParams& p, int grid, int smem, cudaStream_t s) {
-  static int configured = 0;
+static cudaError_t grid_for(uint32_t ntiles, int smem, int* grid) {
+  static int configured = 0, cached_smem = -1, cached_dev = -1, cached_sms = 0, cached_per = 0;
   if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(k_apply<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  k_apply<R, MODE><<<grid, 256, smem, s>>>(p);
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev == cached_dev && smem == cached_smem) {
+    sms = cached_sms;
+    per = cached_per;
+  } else {
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply<R, MODE>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    cached_dev = dev;
+    cached_smem = smem;
+    cached_sms = sms;
+    cached_per = per;
+  }
+  if (per < 1) per = 1;
+  const uint64_t g = (uint64_t)sms * (uint64_t)per;
+  *grid = (int)(g < ntiles ? g : ntiles);
+  return cudaSuccess;
+}
+
+template <typename R, int MODE>
+static cudaError_t launch_one(const ApplyParams& p, int smem, cudaStream_t s) {
+  int grid = 0;
+  cudaError_t e = grid_for<R, MODE>(p.ntiles, smem, &grid);
+  if (e != cudaSuccess) return e;
+  k_apply<R, MODE><<<grid, kThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
 template <typename R>
-static cudaError_t launch_prec(const ApplyParams& p, int grid, int smem, cudaStream_t s) {
+static cudaError_t launch_prec(const ApplyParams& p, int smem, cudaStream_t s) {
   switch (p.mode) {
-    case MODE_PARTIAL: return launch_one<R, MODE_PARTIAL>(p, grid, smem, s);
-    case MODE_STEP: return launch_one<R, MODE_STEP>(p, grid, smem, s);
-    case MODE_RK4: return launch_one<R, MODE_RK4>(p, grid, smem, s);
-    case MODE_DERIV: return launch_one<R, MODE_DERIV>(p, grid, smem, s);
-    case MODE_ENERGY: return launch_one<R, MODE_ENERGY>(p, grid, smem, s);
+    case MODE_PARTIAL: return launch_one<R, MODE_PARTIAL>(p, smem, s);
+    case MODE_STEP: return launch_one<R, MODE_STEP>(p, smem, s);
+    case MODE_RK4: return launch_one<R, MODE_RK4>(p, smem, s);
+    case MODE_DERIV: return launch_one<R, MODE_DERIV>(p, smem, s);
+    case MODE_ENERGY: return launch_one<R, MODE_ENERGY>(p, smem, s);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_apply(int prec, const ApplyParams& p, int grid, int smem, cudaStream_t s) {
-  return prec == 0 ? launch_prec<double>(p, grid, smem, s) : launch_prec<float>(p, grid, smem, s);
+cudaError_t launch_apply(int prec, const ApplyParams& p, int smem, cudaStream_t s) {
+  return prec == 0 ? launch_prec<double>(p, smem, s) : launch_prec<float>(p, smem, s);
+}
+
+// per-index clause counts of one class (computed once per Hamiltonian)
+__global__ void k_diag_codes(uint8_t* out, uint64_t N, const DevTables* tab, int cls) {
+  const DevClass cl = tab->classes[cls];
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = (uint8_t)clause_count<float>(tab, cl, (uint32_t)i);
+}
+
+cudaError_t launch_diag_codes(uint8_t* out, uint64_t N, const DevTables* tab, int cls, cudaStream_t s) {
+  const int grid = (int)((N + 255) / 256 < 8192 ? (N + 255) / 256 : 8192);
+  k_diag_codes<<<grid, 256, 0, s>>>(out, N, tab, cls);
+  return cudaGetLastError();
 }
 
 // ---- pointwise kernels ------------------------------------------------------------------
@@ -389,12 +563,20 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_norm2(const typename Cplx<R>::T* a, uint64_t N, double* partials,
                                                unsigned* counter, double* slots) {
   using C2 = typename Cplx<R>::T;
-  __shared__ double s_red[8];
+  __shared__ double s_red[8 + 2];
   double v[1] = {0.0};
+  R part = (R)0;  // state-precision partial over 16 elements, then FP64
+  int cnt = 0;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
     const C2 x = a[i];
-    v[0] += (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+    part += x.x * x.x + x.y * x.y;
+    if (++cnt == 16) {
+      v[0] += (double)part;
+      part = (R)0;
+      cnt = 0;
+    }
   }
+  v[0] += (double)part;
   if (grid_reduce<1>(v, partials, counter, s_red)) slots[kSlotNorm2] = v[0];
 }
 

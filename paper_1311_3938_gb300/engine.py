@@ -90,6 +90,12 @@ class Context:
             N.aqc_set_initial_state(self.handle, N.AQC_INIT_UNIFORM, 0, 0)
         elif isinstance(state, (int, np.integer)):
             N.aqc_set_initial_state(self.handle, N.AQC_INIT_BASIS, int(state), 0)
+        elif isinstance(state, torch.Tensor) and state.device.type == "cpu":
+            t = state.to(_torch_dtype(self.precision)).contiguous()  # host buffer (pinned: async DMA)
+            if t.numel() != self.N:
+                raise ValueError("state has the wrong length")
+            N.aqc_set_initial_state(self.handle, N.AQC_INIT_USER_HOST, 0, t.data_ptr())
+            self.stream.synchronize()
         elif isinstance(state, torch.Tensor):
             t = state.to(self.dev, _torch_dtype(self.precision)).contiguous()
             if t.numel() != self.N:
@@ -129,6 +135,9 @@ class Context:
 
     def norm2(self):
         return N.aqc_norm2(self.handle)
+
+    def launch_count(self):
+        return N.aqc_launch_count(self.handle)
 
     def hpsi(self, t, psi: torch.Tensor, out: torch.Tensor = None):
         """out = H(t) psi for device tensors of the state dtype."""
