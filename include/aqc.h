@@ -160,10 +160,31 @@ int aqc_norm2(aqc_ctx *ctx, double *out);
  * This is the stand-alone SQH matvec of Sec. I.A. */
 int aqc_hpsi(aqc_ctx *ctx, double t, const void *psi, void *out);
 
+/* ---- entry point that allocates nothing ---------------------------------------------- */
+
+/* Bytes of the library's static device scratch used by aqc_norm2_noalloc (per device). */
+#define AQC_NOALLOC_SCRATCH_BYTES 16384
+
+/* ||psi||^2 (FP64 accumulation) of a caller-owned device vector psi of n_amplitudes
+ * interleaved amplitudes in `precision` (AQC_C128 or AQC_C64), written to the host double *out.
+ * The paper has no counterpart: this is a service for callers that may not allocate device
+ * memory -- code running inside another framework's memory pool or allocator, plugins whose
+ * host application owns all GPU memory, or work issued where cudaMalloc is not allowed.  It
+ * needs no context and no workspace and calls no allocating routine: its reduction scratch is a
+ * static device array of AQC_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library
+ * holds until exit.  It runs on the calling thread's current device (psi must live there) and
+ * on `cuda_stream`, and synchronises that stream.  The first call on a device looks up the
+ * scratch address once; make that first call before any stream capture.  All calls on a
+ * device share the scratch, so calls that overlap on the GPU (different streams or threads
+ * without ordering) race and give wrong results.  n_amplitudes must be in [1, 2^31]; larger
+ * sizes are rejected with AQC_E_INVAL; errors are described by aqc_last_error(NULL). */
+int aqc_norm2_noalloc(int precision, const void *psi, uint64_t n_amplitudes, void *cuda_stream, double *out);
+
 /* Total kernel launches the context has issued since creation (monotone counter). */
 int aqc_launch_count(const aqc_ctx *ctx, int64_t *out);
 
-/* Message of the last error of ctx (or of the last failed aqc_create if ctx is NULL). */
+/* Message of the last error of ctx (or, for ctx == NULL, of the last failed aqc_create or
+ * aqc_norm2_noalloc on the calling thread). */
 const char *aqc_last_error(const aqc_ctx *ctx);
 
 /* Library version string. */

@@ -440,6 +440,10 @@ int read_slot(aqc_ctx* c, int slot, double* out) {
 
 }  // namespace
 
+namespace aqc {
+void set_global_error(const char* msg) { g_create_error = msg; }
+}  // namespace aqc
+
 extern "C" {
 
 size_t aqc_workspace_bytes(int n_qubits, int precision) {
