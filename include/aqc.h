@@ -160,6 +160,48 @@ int aqc_norm2(aqc_ctx *ctx, double *out);
  * This is the stand-alone SQH matvec of Sec. I.A. */
 int aqc_hpsi(aqc_ctx *ctx, double t, const void *psi, void *out);
 
+/* ---- batches: many states stepped per launch ---------------------------------------- */
+/* A batch steps many contexts of one device and precision together: each batched launch
+ * processes (member, tile) work items of all members, so small states share the GPU, and K
+ * PEC grid steps (Sec. I.B) are captured once in a CUDA graph and replayed.  Every member
+ * keeps its own Hamiltonian, schedule, step grid and state; its arithmetic is the same as in
+ * aqc_propagate, so a member's result does not depend on the other members.  While a context
+ * is a member it must not be used directly; aqc_batch_remove hands it back (its step count,
+ * ||psi||^2 and error estimates updated) for aqc_fidelity / aqc_energy / aqc_get_state. */
+typedef struct aqc_batch aqc_batch;
+
+/* Workspace bytes for a batch of up to max_members members and max_items work items per
+ * layout level (a member contributes 2^(n - tile_bits) items per level).  0 if invalid. */
+size_t aqc_batch_workspace_bytes(int max_members, int64_t max_items);
+
+/* Create a batch; `workspace` is caller-owned device memory (256-byte aligned) of at least
+ * aqc_batch_workspace_bytes() bytes; cuda_stream NULL makes the batch create its own stream. */
+int aqc_batch_create(aqc_batch **out, int device, int precision, int max_members, int64_t max_items, void *workspace,
+                     size_t workspace_bytes, void *cuda_stream);
+void aqc_batch_destroy(aqc_batch *b);
+
+/* Launch shape: threads per CTA (128 or 256) and PEC steps per graph replay (1..4096). */
+int aqc_batch_set_shape(aqc_batch *b, int threads, int steps_per_round);
+
+/* Add a context that has a Hamiltonian, a schedule and an initial state; its RK4 start-up
+ * runs now on the batch stream.  *slot_out receives its slot. */
+int aqc_batch_add(aqc_batch *b, aqc_ctx *ctx, int *slot_out);
+
+/* Remove the member in `slot` and hand its context back. */
+int aqc_batch_remove(aqc_batch *b, int slot);
+
+/* Enqueue `rounds` graph replays: every member advances by up to rounds * steps_per_round
+ * grid steps and stops at its own t = T.  Asynchronous. */
+int aqc_batch_run(aqc_batch *b, int64_t rounds);
+
+/* Synchronise the batch stream; steps_done[slot] (array of max_members, may be NULL) gets each
+ * member's completed grid steps (-1 for a free slot), *active_out the members not yet at T,
+ * *launches_out the kernel launches issued so far. */
+int aqc_batch_poll(aqc_batch *b, int64_t *steps_done, int *active_out, int64_t *launches_out);
+
+/* Message of the last error of b (or of the last failed aqc_batch_create if b is NULL). */
+const char *aqc_batch_last_error(const aqc_batch *b);
+
 /* ---- entry point that allocates nothing ---------------------------------------------- */
 
 /* Bytes of the library's static device scratch used by aqc_norm2_noalloc (per device). */

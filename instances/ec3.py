@@ -147,8 +147,8 @@ def _draw_triple(rng: SplitMix64, n: int):
 
 def generate_ec3(n: int, seed: int, max_restarts: int = 1000) -> EC3Instance:
     """Seeded EC3 instance with a unique satisfying assignment."""
-    if n < 3 or n > 40:
-        raise ValueError("n must be in [3, 40]")
+    if n < 4 or n > 40:
+        raise ValueError("n must be in [4, 40] (three bits admit one clause and three solutions)")
     rng = SplitMix64(seed)
     pool = comb(n, 3)
     for restart in range(max_restarts):

@@ -82,6 +82,16 @@ def lib():
             "aqc_norm2": (i32, [vp, C.POINTER(dbl)]),
             "aqc_hpsi": (i32, [vp, dbl, vp, vp]),
             "aqc_launch_count": (i32, [vp, C.POINTER(i64)]),
+            "aqc_batch_workspace_bytes": (sz, [i32, i64]),
+            "aqc_batch_create": (i32, [C.POINTER(vp), i32, i32, i32, i64, vp, sz, vp]),
+            "aqc_batch_destroy": (None, [vp]),
+            "aqc_batch_set_shape": (i32, [vp, i32, i32]),
+            "aqc_batch_add": (i32, [vp, vp, C.POINTER(i32)]),
+            "aqc_batch_remove": (i32, [vp, i32]),
+            "aqc_batch_run": (i32, [vp, i64]),
+            "aqc_batch_poll": (i32, [vp, vp, C.POINTER(i32), C.POINTER(i64)]),
+            "aqc_batch_last_error": (C.c_char_p, [vp]),
+            "aqc_norm2_noalloc": (i32, [i32, vp, u64, vp, C.POINTER(dbl)]),
             "aqc_last_error": (C.c_char_p, [vp]),
             "aqc_version": (C.c_char_p, []),
         }
@@ -188,6 +198,62 @@ def aqc_hpsi(ctx, t, psi_ptr, out_ptr):
 def aqc_launch_count(ctx):
     out = C.c_int64()
     _check(ctx, lib().aqc_launch_count(ctx, C.byref(out)))
+    return out.value
+
+
+def _bcheck(b, rc):
+    if rc != AQC_OK:
+        msg = lib().aqc_batch_last_error(b)
+        raise AqcError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def aqc_batch_workspace_bytes(max_members: int, max_items: int) -> int:
+    return int(lib().aqc_batch_workspace_bytes(max_members, max_items))
+
+
+def aqc_batch_create(device, precision, max_members, max_items, workspace, workspace_bytes, stream):
+    h = C.c_void_p()
+    rc = lib().aqc_batch_create(C.byref(h), device, precision, max_members, max_items, C.c_void_p(workspace),
+                                workspace_bytes, C.c_void_p(stream) if stream else None)
+    _bcheck(None, rc)
+    return h
+
+
+def aqc_batch_destroy(b):
+    lib().aqc_batch_destroy(b)
+
+
+def aqc_batch_set_shape(b, threads, steps_per_round):
+    _bcheck(b, lib().aqc_batch_set_shape(b, int(threads), int(steps_per_round)))
+
+
+def aqc_batch_add(b, ctx):
+    slot = C.c_int()
+    _bcheck(b, lib().aqc_batch_add(b, ctx, C.byref(slot)))
+    return slot.value
+
+
+def aqc_batch_remove(b, slot):
+    _bcheck(b, lib().aqc_batch_remove(b, int(slot)))
+
+
+def aqc_batch_run(b, rounds):
+    _bcheck(b, lib().aqc_batch_run(b, int(rounds)))
+
+
+def aqc_batch_poll(b, max_members):
+    steps = (C.c_int64 * max_members)()
+    active = C.c_int()
+    launches = C.c_int64()
+    _bcheck(b, lib().aqc_batch_poll(b, steps, C.byref(active), C.byref(launches)))
+    return list(steps), active.value, launches.value
+
+
+def aqc_norm2_noalloc(precision, psi_ptr, n_amplitudes, stream):
+    out = C.c_double()
+    _check(None, lib().aqc_norm2_noalloc(int(precision), C.c_void_p(psi_ptr), int(n_amplitudes),
+                                         C.c_void_p(stream) if stream else None, C.byref(out)))
     return out.value
 
 

@@ -440,6 +440,161 @@ int read_slot(aqc_ctx* c, int slot, double* out) {
 
 }  // namespace
 
+
+// ---------------------------------------------------------------------------------------
+// Batches: many contexts stepped together by k_batch, K PEC steps per CUDA-graph replay.
+// ---------------------------------------------------------------------------------------
+struct aqc_batch {
+  int device = 0, prec = 0, max_members = 0;
+  int64_t max_items = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  char* ws = nullptr;
+  BatchInst* d_insts = nullptr;
+  BatchItem* d_items[kMaxLayouts] = {nullptr};
+  double* d_partials = nullptr;
+  std::vector<aqc_ctx*> members;   // slot -> context (nullptr = free)
+  std::vector<int64_t> step_at_add;
+  std::vector<BatchInst> h_insts;  // host copy (refreshed by poll / rebuild)
+  int nitems[kMaxLayouts] = {0};
+  int smem[kMaxLayouts] = {0};
+  int nlevels = 0;
+  bool dirty = true;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int threads = 256, steps_per_round = 16;
+  int64_t launches = 0;
+  std::string err;
+};
+
+namespace {
+
+struct BatchPlan {
+  size_t off_insts, off_items, off_partials, total;
+};
+
+BatchPlan plan_batch(int max_members, int64_t max_items) {
+  BatchPlan b;
+  b.off_insts = 0;
+  b.off_items = align_up((size_t)max_members * sizeof(BatchInst), 256);
+  b.off_partials = align_up(b.off_items + (size_t)kMaxLayouts * (size_t)max_items * sizeof(BatchItem), 256);
+  b.total = align_up(b.off_partials + (size_t)max_items * 2 * sizeof(double), 256);
+  return b;
+}
+
+#define BFAIL(b, code, ...)                    \
+  do {                                         \
+    char buf_[512];                            \
+    snprintf(buf_, sizeof(buf_), __VA_ARGS__); \
+    (b)->err = buf_;                           \
+    return (code);                             \
+  } while (0)
+
+#define BCUDA(b, expr)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) BFAIL(b, AQC_E_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+void fill_inst(const aqc_ctx* c, BatchInst* I) {
+  memset(I, 0, sizeof(*I));
+  I->tab = c->d_tab;
+  I->dcode = c->table_class >= 0 ? c->d_dcode : nullptr;
+  for (int v = 0; v < kVecCount; v++) I->vec[v] = c->vec[v];
+  I->nl = (int)c->layouts.size();
+  for (int l = 0; l < I->nl; l++) I->layouts[l] = c->layouts[l];
+  I->s_kind = c->s_kind;
+  I->T = c->T;
+  I->h = c->h;
+  for (int g = 0; g < 3; g++)
+    for (int k = 0; k < 4; k++) I->poly[g][k] = c->poly[g][k];
+  I->step = c->step;
+  I->nsteps = c->nsteps;
+}
+
+int batch_pull(aqc_batch* b) {
+  if (b->max_members == 0) return AQC_OK;
+  BCUDA(b, cudaMemcpyAsync(b->h_insts.data(), b->d_insts, sizeof(BatchInst) * b->max_members, cudaMemcpyDeviceToHost,
+                           b->stream));
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  return AQC_OK;
+}
+
+void drop_graph(aqc_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+}
+
+// work lists + per-level shared memory + one captured graph of K batched grid steps
+int batch_rebuild(aqc_batch* b) {
+  int rc = batch_pull(b);
+  if (rc) return rc;
+  std::vector<BatchItem> items[kMaxLayouts];
+  int smem[kMaxLayouts] = {0};
+  int nlev = 0;
+  for (int slot = 0; slot < b->max_members; slot++) {
+    aqc_ctx* c = b->members[slot];
+    if (!c) continue;
+    BatchInst& I = b->h_insts[slot];
+    const int nl = (int)c->layouts.size();
+    nlev = std::max(nlev, nl);
+    for (int l = 0; l < nl; l++) {
+      const uint32_t ntiles = 1u << (c->n - c->layouts[l].t);
+      if (l == 0) I.item_begin = (uint32_t)items[0].size();
+      for (uint32_t t = 0; t < ntiles; t++) items[l].push_back(BatchItem{(uint32_t)slot, t});
+      if (l == 0) I.item_end = (uint32_t)items[0].size();
+      const bool first = (l == nl - 1);
+      const size_t sm = apply_smem_bytes(c->prec, c->layouts[l].t, c->nplain[l],
+                                         c->ngeneral[l] + (first ? c->n_remote : 0), first ? c->n_z : 0);
+      if (sm > 227 * 1024) BFAIL(b, AQC_E_UNSUPPORTED, "shared memory %zu bytes too large", sm);
+      smem[l] = std::max(smem[l], (int)sm);
+    }
+    I.ticket = 0;
+  }
+  for (int l = 0; l < nlev; l++) {
+    if ((int64_t)items[l].size() > b->max_items) BFAIL(b, AQC_E_NOMEM, "batch needs %zu work items > max_items", items[l].size());
+    if (!items[l].empty())
+      BCUDA(b, cudaMemcpyAsync(b->d_items[l], items[l].data(), items[l].size() * sizeof(BatchItem),
+                               cudaMemcpyHostToDevice, b->stream));
+    b->nitems[l] = (int)items[l].size();
+    b->smem[l] = smem[l];
+  }
+  for (int l = nlev; l < kMaxLayouts; l++) b->nitems[l] = 0;
+  b->nlevels = nlev;
+  BCUDA(b, cudaMemcpyAsync(b->d_insts, b->h_insts.data(), sizeof(BatchInst) * b->max_members, cudaMemcpyHostToDevice,
+                           b->stream));
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  drop_graph(b);
+  if (nlev > 0) {
+    BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < b->steps_per_round && e == cudaSuccess; k++) {
+      for (int l = nlev - 1; l >= 0 && e == cudaSuccess; l--) {
+        BatchLaunch bl;
+        bl.items = b->d_items[l];
+        bl.insts = b->d_insts;
+        bl.partials = b->d_partials;
+        bl.level = l;
+        e = launch_batch(b->prec, b->threads, bl, b->nitems[l], b->smem[l], b->stream);
+      }
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      BFAIL(b, AQC_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    b->graph = g;
+    BCUDA(b, cudaGraphInstantiate(&b->gexec, g, 0));
+  }
+  b->dirty = false;
+  return AQC_OK;
+}
+
+}  // namespace
+
 namespace aqc {
 void set_global_error(const char* msg) { g_create_error = msg; }
 }  // namespace aqc
@@ -763,6 +918,190 @@ int aqc_hpsi(aqc_ctx* ctx, double t, const void* psi, void* out) {
   fin.mode = MODE_PARTIAL;
   return evaluate(ctx, w, psi, fin, out);
 }
+
+
+size_t aqc_batch_workspace_bytes(int max_members, int64_t max_items) {
+  if (max_members < 1 || max_members > 65536 || max_items < 1 || max_items > ((int64_t)1 << 28)) return 0;
+  return plan_batch(max_members, max_items).total;
+}
+
+int aqc_batch_create(aqc_batch** out, int device, int precision, int max_members, int64_t max_items, void* workspace,
+                     size_t workspace_bytes, void* cuda_stream) {
+  if (!out) return AQC_E_INVAL;
+  *out = nullptr;
+  if (precision != AQC_C128 && precision != AQC_C64) {
+    g_create_error = "precision must be AQC_C128 or AQC_C64";
+    return AQC_E_INVAL;
+  }
+  const size_t need = aqc_batch_workspace_bytes(max_members, max_items);
+  if (need == 0) {
+    g_create_error = "max_members must be in [1, 65536] and max_items in [1, 2^28]";
+    return AQC_E_INVAL;
+  }
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255u)) {
+    g_create_error = "batch workspace missing, unaligned or smaller than aqc_batch_workspace_bytes()";
+    return AQC_E_NOMEM;
+  }
+  aqc_batch* b = new (std::nothrow) aqc_batch();
+  if (!b) return AQC_E_NOMEM;
+  b->device = device;
+  b->prec = precision;
+  b->max_members = max_members;
+  b->max_items = max_items;
+  b->ws = (char*)workspace;
+  const BatchPlan bp = plan_batch(max_members, max_items);
+  b->d_insts = (BatchInst*)(b->ws + bp.off_insts);
+  for (int l = 0; l < kMaxLayouts; l++)
+    b->d_items[l] = (BatchItem*)(b->ws + bp.off_items + (size_t)l * (size_t)max_items * sizeof(BatchItem));
+  b->d_partials = (double*)(b->ws + bp.off_partials);
+  b->members.assign(max_members, nullptr);
+  b->step_at_add.assign(max_members, 0);
+  b->h_insts.assign(max_members, BatchInst());
+  memset(b->h_insts.data(), 0, sizeof(BatchInst) * max_members);
+  DeviceGuard dg(device);
+  if (cuda_stream) {
+    b->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      g_create_error = "cudaStreamCreateWithFlags failed";
+      return AQC_E_CUDA;
+    }
+    b->own_stream = true;
+  }
+  if (cudaMemsetAsync(b->d_insts, 0, sizeof(BatchInst) * max_members, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    g_create_error = "cudaMemsetAsync on the batch workspace failed";
+    return AQC_E_CUDA;
+  }
+  *out = b;
+  return AQC_OK;
+}
+
+void aqc_batch_destroy(aqc_batch* b) {
+  if (!b) return;
+  DeviceGuard dg(b->device);
+  cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+int aqc_batch_set_shape(aqc_batch* b, int threads, int steps_per_round) {
+  if (!b) return AQC_E_INVAL;
+  if (threads != 128 && threads != 256) BFAIL(b, AQC_E_INVAL, "threads must be 128 or 256");
+  if (steps_per_round < 1 || steps_per_round > 4096) BFAIL(b, AQC_E_INVAL, "steps_per_round must be in [1, 4096]");
+  b->threads = threads;
+  b->steps_per_round = steps_per_round;
+  b->dirty = true;
+  return AQC_OK;
+}
+
+int aqc_batch_add(aqc_batch* b, aqc_ctx* c, int* slot_out) {
+  if (!b || !c) return AQC_E_INVAL;
+  if (c->device != b->device || c->prec != b->prec) BFAIL(b, AQC_E_INVAL, "context device/precision differ from the batch");
+  if (!c->have_state) BFAIL(b, AQC_E_STATE, "context has no initial state");
+  for (aqc_ctx* m : b->members)
+    if (m == c) BFAIL(b, AQC_E_INVAL, "context is already a member");
+  int slot = -1;
+  for (int i = 0; i < b->max_members; i++)
+    if (!b->members[i]) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) BFAIL(b, AQC_E_NOMEM, "batch is full (%d members)", b->max_members);
+  DeviceGuard dg(b->device);
+  int rc = ensure_ready(c);
+  if (rc) BFAIL(b, rc, "member: %s", c->err.c_str());
+  if (c->nsteps == 0) {
+    c->nsteps = c->nsteps_req > 0 ? c->nsteps_req : rule_steps(c);
+    c->h = c->T / (double)c->nsteps;
+  }
+  // start-up on the batch stream: RK4 steps, f_3 and the first predictor (after the
+  // context's own queued work, e.g. its initial state)
+  BCUDA(b, cudaStreamSynchronize(c->stream));
+  cudaStream_t saved = c->stream;
+  c->stream = b->stream;
+  while (rc == 0 && c->step < 3 && c->step < c->nsteps) rc = rk4_step(c);
+  if (rc == 0 && c->step >= 3 && c->step < c->nsteps && !c->hist_ready) rc = start_history(c);
+  c->stream = saved;
+  if (rc) BFAIL(b, rc, "member start-up: %s", c->err.c_str());
+  rc = batch_pull(b);
+  if (rc) return rc;
+  fill_inst(c, &b->h_insts[slot]);
+  BCUDA(b, cudaMemcpyAsync(b->d_insts + slot, &b->h_insts[slot], sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  b->members[slot] = c;
+  b->step_at_add[slot] = c->step;
+  b->dirty = true;
+  if (slot_out) *slot_out = slot;
+  return AQC_OK;
+}
+
+int aqc_batch_remove(aqc_batch* b, int slot) {
+  if (!b) return AQC_E_INVAL;
+  if (slot < 0 || slot >= b->max_members || !b->members[slot]) BFAIL(b, AQC_E_INVAL, "no member in slot %d", slot);
+  DeviceGuard dg(b->device);
+  int rc = batch_pull(b);
+  if (rc) return rc;
+  aqc_ctx* c = b->members[slot];
+  const BatchInst& I = b->h_insts[slot];
+  c->evals += I.step - b->step_at_add[slot];
+  c->step = I.step;
+  if (c->step >= 3) c->hist_ready = true;
+  // carry the member's reductions into the context's result slots
+  double sl[3] = {I.norm2, I.max_err, I.last_err};
+  if (I.step > b->step_at_add[slot]) {
+    cudaMemcpyAsync(c->d_slots + kSlotNorm2, &sl[0], sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    cudaMemcpyAsync(c->d_slots + kSlotMaxErr, &sl[1], sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    cudaMemcpyAsync(c->d_slots + kSlotLastErr, &sl[2], sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+  }
+  b->members[slot] = nullptr;
+  memset(&b->h_insts[slot], 0, sizeof(BatchInst));
+  BCUDA(b, cudaMemcpyAsync(b->d_insts + slot, &b->h_insts[slot], sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  b->dirty = true;
+  return AQC_OK;
+}
+
+int aqc_batch_run(aqc_batch* b, int64_t rounds) {
+  if (!b) return AQC_E_INVAL;
+  if (rounds < 0) BFAIL(b, AQC_E_INVAL, "rounds must be >= 0");
+  DeviceGuard dg(b->device);
+  if (b->dirty) {
+    int rc = batch_rebuild(b);
+    if (rc) return rc;
+  }
+  if (!b->gexec) return AQC_OK;
+  int per = 0;
+  for (int l = 0; l < b->nlevels; l++) per += b->nitems[l] > 0 ? 1 : 0;
+  for (int64_t r = 0; r < rounds; r++) {
+    BCUDA(b, cudaGraphLaunch(b->gexec, b->stream));
+    b->launches += (int64_t)per * b->steps_per_round;
+  }
+  return AQC_OK;
+}
+
+int aqc_batch_poll(aqc_batch* b, int64_t* steps_done, int* active_out, int64_t* launches_out) {
+  if (!b) return AQC_E_INVAL;
+  DeviceGuard dg(b->device);
+  int rc = batch_pull(b);
+  if (rc) return rc;
+  int active = 0;
+  for (int i = 0; i < b->max_members; i++) {
+    const aqc_ctx* c = b->members[i];
+    if (steps_done) steps_done[i] = c ? b->h_insts[i].step : -1;
+    if (c && b->h_insts[i].step < b->h_insts[i].nsteps) active++;
+  }
+  if (active_out) *active_out = active;
+  if (launches_out) *launches_out = b->launches;
+  return AQC_OK;
+}
+
+const char* aqc_batch_last_error(const aqc_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
 
 int aqc_launch_count(const aqc_ctx* ctx, int64_t* out) {
   if (!ctx || !out) return AQC_E_INVAL;

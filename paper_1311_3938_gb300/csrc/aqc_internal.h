@@ -93,6 +93,39 @@ struct ApplyParams {
   double* slots;     // results: see kSlot*
 };
 
+// vectors of a state (workspace order)
+constexpr int kVecY = 0, kVecP = 1, kVecQ = 2, kVecF0 = 3, kVecAcc = 7, kVecCount = 8;
+
+// One member of a batch: everything its PEC steps need, read by the batched kernel on the device.
+struct BatchInst {
+  const DevTables* tab;
+  const uint8_t* dcode;  // nullable
+  void* vec[kVecCount];
+  Layout layouts[kMaxLayouts];
+  int nl;
+  int s_kind;
+  double T, h;
+  double poly[3][4];
+  int64_t step;    // next PEC step n (computes f_{n+1}); advanced by the member's last CTA
+  int64_t nsteps;
+  uint32_t item_begin, item_end;  // the member's items in the level-0 work list
+  unsigned ticket;
+  int pad;
+  double norm2, max_err, last_err;
+};
+
+struct BatchItem {
+  uint32_t inst;
+  uint32_t tile;
+};
+
+struct BatchLaunch {
+  const BatchItem* items;
+  BatchInst* insts;
+  double* partials;  // two doubles per level-0 item
+  int level;
+};
+
 // result slots (doubles) in the workspace
 constexpr int kSlotNorm2 = 0;
 constexpr int kSlotMaxErr = 1;
@@ -112,5 +145,6 @@ cudaError_t launch_reduce(int prec, int what, const void* a, uint64_t N, double*
                           double* slots, int grid, cudaStream_t s);
 cudaError_t launch_fidelity(int prec, const void* a, uint64_t w, double* slots, cudaStream_t s);
 int reduce_grid(uint64_t N);
+cudaError_t launch_batch(int prec, int threads, const BatchLaunch& b, int nitems, int smem, cudaStream_t s);
 
 }  // namespace aqc

@@ -173,42 +173,64 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <typename R, int MODE>
-__global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
+// Everything one tile pass needs, built per CTA from a single-instance launch (ApplyParams) or
+// from one batch member (BatchInst).
+template <typename R>
+struct TileCtx {
   using C2 = typename Cplx<R>::T;
-  extern __shared__ __align__(16) unsigned char smem[];
+  Layout L;
+  uint32_t tsize, tmask;
+  int np, ngl, ng, nz, ncls, tcls, stage;
+  R dconst, wtab, h;
+  const DevTables* tab;
+  const uint8_t* dcode;
+  double w0, w1, w2;
+  const C2 *src, *qin, *f0, *f1, *f2;
+  C2 *qout, *y, *fout, *pout, *acc;
+  C2* s_p;
+  PFlip<R>* s_pf;
+  SFlip<R>* s_gf;
+  SZ<R>* s_z;
+  double* s_red;
+};
 
-  const Layout L = P.L;
-  const uint32_t tsize = 1u << L.t;
-  const uint32_t tmask = tsize - 1u;
-  const DevTables* __restrict__ tab = P.tab;
-  const int li = P.layout_index;
+__device__ __forceinline__ double pick3(double a, double b, double c, int g) { return g == 0 ? a : (g == 1 ? b : c); }
+
+// Effective coefficients of layout li at weights (w0, w1, w2) into shared memory (once per CTA).
+template <typename R>
+__device__ __forceinline__ void load_coefficients(TileCtx<R>& T, const DevTables* __restrict__ tab, const Layout& L,
+                                                  int li, bool with_diag, bool with_remote, const uint8_t* dcode,
+                                                  double w0, double w1, double w2, unsigned char* smem) {
+  T.L = L;
+  T.tsize = 1u << L.t;
+  T.tmask = T.tsize - 1u;
+  T.tab = tab;
+  T.w0 = w0;
+  T.w1 = w1;
+  T.w2 = w2;
   const int fb = tab->flip_begin[li];
-  const int np = tab->plain_count[li];
-  const int ngl = tab->flip_begin[li + 1] - fb - np;
+  T.np = tab->plain_count[li];
+  T.ngl = tab->flip_begin[li + 1] - fb - T.np;
   const int rb = tab->flip_begin[tab->n_layouts];
-  const int nrem = P.with_remote ? tab->n_remote : 0;
-  const int ng = ngl + nrem;
-  const int nz = P.with_diag ? tab->n_z : 0;
-  const SmemMap<R> map(tsize, np, ng, nz);
-
-  C2* s_p = reinterpret_cast<C2*>(smem);
-  PFlip<R>* s_pf = reinterpret_cast<PFlip<R>*>(smem + map.pf);
-  SFlip<R>* s_gf = reinterpret_cast<SFlip<R>*>(smem + map.gf);
-  SZ<R>* s_z = reinterpret_cast<SZ<R>*>(smem + map.zs);
-  double* s_red = reinterpret_cast<double*>(smem + map.red);
-
-  // effective coefficients at this evaluation time
-  for (int k = threadIdx.x; k < np; k += blockDim.x) {
+  const int nrem = with_remote ? tab->n_remote : 0;
+  T.ng = T.ngl + nrem;
+  T.nz = with_diag ? tab->n_z : 0;
+  const SmemMap<R> map(T.tsize, T.np, T.ng, T.nz);
+  T.s_p = reinterpret_cast<typename TileCtx<R>::C2*>(smem);
+  T.s_pf = reinterpret_cast<PFlip<R>*>(smem + map.pf);
+  T.s_gf = reinterpret_cast<SFlip<R>*>(smem + map.gf);
+  T.s_z = reinterpret_cast<SZ<R>*>(smem + map.zs);
+  T.s_red = reinterpret_cast<double*>(smem + map.red);
+  for (int k = threadIdx.x; k < T.np; k += blockDim.x) {
     const DevFlip d = tab->flips[fb + k];
     PFlip<R> f;
     f.lx = d.lx;
-    f.c = (R)(d.coef * P.w[d.group]);
-    s_pf[k] = f;
+    f.c = (R)(d.coef * pick3(w0, w1, w2, d.group));
+    T.s_pf[k] = f;
   }
-  for (int k = threadIdx.x; k < ng; k += blockDim.x) {
-    const DevFlip d = tab->flips[k < ngl ? fb + np + k : rb + (k - ngl)];
-    const double c = d.coef * P.w[d.group];
+  for (int k = threadIdx.x; k < T.ng; k += blockDim.x) {
+    const DevFlip d = tab->flips[k < T.ngl ? fb + T.np + k : rb + (k - T.ngl)];
+    const double c = d.coef * pick3(w0, w1, w2, d.group);
     double cr = 0.0, ci = 0.0;
     switch (d.ipow & 3) {
       case 0: cr = c; break;
@@ -217,44 +239,55 @@ __global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
       default: ci = -c; break;
     }
     SFlip<R> f;
-    f.lx = k < ngl ? d.lx : 0u;
+    f.lx = k < T.ngl ? d.lx : 0u;
     f.x = d.x;
     f.zm = d.zm;
     f.cplx = (d.ipow & 1);
     f.cr = (R)cr;
     f.ci = (R)ci;
-    s_gf[k] = f;
+    T.s_gf[k] = f;
   }
-  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+  for (int k = threadIdx.x; k < T.nz; k += blockDim.x) {
     SZ<R> e;
     e.zm = tab->z[k].zm;
     e.pad = 0;
-    e.c = (R)(tab->z[k].coef * P.w[tab->z[k].group]);
-    s_z[k] = e;
+    e.c = (R)(tab->z[k].coef * pick3(w0, w1, w2, tab->z[k].group));
+    T.s_z[k] = e;
   }
-  R dconst = (R)0, wtab = (R)0;
-  int tcls = -1, ncls = 0;
-  if (P.with_diag) {
-    dconst = (R)(tab->ident[0] * P.w[0] + tab->ident[1] * P.w[1] + tab->ident[2] * P.w[2]);
-    ncls = tab->n_classes;
-    if (P.dcode) {
-      tcls = tab->table_class;
-      wtab = (R)(tab->classes[tcls].scale * P.w[tab->classes[tcls].group]);
+  T.dconst = (R)0;
+  T.wtab = (R)0;
+  T.tcls = -1;
+  T.ncls = 0;
+  T.dcode = nullptr;
+  if (with_diag) {
+    T.dconst = (R)(tab->ident[0] * w0 + tab->ident[1] * w1 + tab->ident[2] * w2);
+    T.ncls = tab->n_classes;
+    if (dcode && tab->table_class >= 0) {
+      T.tcls = tab->table_class;
+      T.dcode = dcode;
+      T.wtab = (R)(tab->classes[T.tcls].scale * pick3(w0, w1, w2, tab->classes[T.tcls].group));
     }
   }
+}
 
-  const C2* __restrict__ src = reinterpret_cast<const C2*>(P.src);
-  double red[2] = {0.0, 0.0};
-  const R h = (R)P.h;
+// One tile: stage the source tile in shared memory, then for every point of the tile compute
+// acc = q + diagonal + products, and run the mode epilogue.  rt0/rt1 collect the reduction
+// partials of this thread in the state precision.
+template <typename R, int MODE>
+__device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile, R& rt0, R& rt1) {
+  using C2 = typename Cplx<R>::T;
   constexpr bool kNeedY = (MODE == MODE_STEP || MODE == MODE_RK4);
   constexpr bool kNeedF = (MODE == MODE_STEP);
-  const C2 zero2 = C2{(R)0, (R)0};
   constexpr int kV = sizeof(R) == 4 ? kVf : kVd;
-  // persistent CTAs: one prologue and one reduction per CTA, tiles taken round-robin
-  for (uint32_t tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
+  const C2 zero2 = C2{(R)0, (R)0};
+  const Layout L = T.L;
+  const uint32_t tsize = T.tsize, tmask = T.tmask;
+  const C2* __restrict__ src = T.src;
+  C2* s_p = T.s_p;
+
   // stage the source tile with asynchronous 16-byte copies: a pair of consecutive indices for
   // complex64 (tile bit 0 is global bit 0), one index for complex128
-  __syncthreads();  // readers of the previous tile are done
+  __syncthreads();  // readers of the previous tile (or of the coefficients' writers) are done
   const uint32_t zb = tile_base(L, tile);
   {
     constexpr uint32_t per16 = 16 / sizeof(C2);  // indices per 16-byte granule
@@ -267,9 +300,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
   }
   __syncthreads();
 
-  // reductions: per-thread partials over one tile in the state precision (a few dozen
-  // points), promoted to FP64 once per tile; FP64 across tiles, CTAs and the grid
-  R rt0 = (R)0, rt1 = (R)0;
   for (uint32_t base = threadIdx.x; base < tsize; base += blockDim.x * kV) {
     uint32_t jm[kV], z[kV];
     bool ok[kV];
@@ -286,15 +316,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
     uint32_t code[kV];
 #pragma unroll
     for (int v = 0; v < kV; v++) {
-      qv[v] = (P.qin && ok[v]) ? reinterpret_cast<const C2*>(P.qin)[z[v]] : zero2;
-      code[v] = (tcls >= 0 && ok[v]) ? (uint32_t)P.dcode[z[v]] : 0u;
-      if (kNeedY) y0[v] = ok[v] ? reinterpret_cast<const C2*>(P.y)[z[v]] : zero2;
+      qv[v] = (T.qin && ok[v]) ? T.qin[z[v]] : zero2;
+      code[v] = (T.tcls >= 0 && ok[v]) ? (uint32_t)T.dcode[z[v]] : 0u;
+      if (kNeedY) y0[v] = ok[v] ? T.y[z[v]] : zero2;
       if (kNeedF) {
-        a[v] = ok[v] ? reinterpret_cast<const C2*>(P.f0)[z[v]] : zero2;
-        b[v] = ok[v] ? reinterpret_cast<const C2*>(P.f1)[z[v]] : zero2;
-        c[v] = ok[v] ? reinterpret_cast<const C2*>(P.f2)[z[v]] : zero2;
+        a[v] = ok[v] ? T.f0[z[v]] : zero2;
+        b[v] = ok[v] ? T.f1[z[v]] : zero2;
+        c[v] = ok[v] ? T.f2[z[v]] : zero2;
       } else if (MODE == MODE_RK4) {
-        a[v] = (ok[v] && P.stage > 1) ? reinterpret_cast<const C2*>(P.acc)[z[v]] : zero2;
+        a[v] = (ok[v] && T.stage > 1) ? T.acc[z[v]] : zero2;
       }
     }
     // 2. X strings with real coefficients: shared-memory gathers
@@ -304,8 +334,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
       ar[v] = (R)0;
       ai[v] = (R)0;
     }
-    for (int k = 0; k < np; k++) {
-      const PFlip<R> f = s_pf[k];
+    for (int k = 0; k < T.np; k++) {
+      const PFlip<R> f = T.s_pf[k];
 #pragma unroll
       for (int v = 0; v < kV; v++) {
         const C2 u = s_p[jm[v] ^ f.lx];
@@ -314,12 +344,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
       }
     }
     // 3. general products (Y/Z phases, complex coefficients) and remote products
-    for (int k = 0; k < ng; k++) {
-      const SFlip<R> f = s_gf[k];
+    for (int k = 0; k < T.ng; k++) {
+      const SFlip<R> f = T.s_gf[k];
 #pragma unroll
       for (int v = 0; v < kV; v++) {
         C2 u;
-        if (k < ngl)
+        if (k < T.ngl)
           u = s_p[jm[v] ^ f.lx];
         else
           u = ok[v] ? src[z[v] ^ f.x] : zero2;
@@ -333,18 +363,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
       }
     }
     // 4. diagonal and partial sum of the earlier layouts
+    const bool with_diag = (T.nz > 0 || T.ncls > 0 || T.dconst != (R)0);
 #pragma unroll
     for (int v = 0; v < kV; v++) {
-      if (P.with_diag) {
-        R d = dconst;
-        if (tcls >= 0) d += wtab * (R)code[v];
-        for (int cc = 0; cc < ncls; cc++) {
-          if (cc == tcls) continue;
-          const DevClass cl = tab->classes[cc];
-          d += (R)(cl.scale * P.w[cl.group]) * clause_count<R>(tab, cl, z[v]);
+      if (with_diag) {
+        R d = T.dconst;
+        if (T.tcls >= 0) d += T.wtab * (R)code[v];
+        for (int cc = 0; cc < T.ncls; cc++) {
+          if (cc == T.tcls) continue;
+          const DevClass cl = T.tab->classes[cc];
+          d += (R)(cl.scale * pick3(T.w0, T.w1, T.w2, cl.group)) * clause_count<R>(T.tab, cl, z[v]);
         }
-        for (int k = 0; k < nz; k++) {
-          const SZ<R> e = s_z[k];
+        for (int k = 0; k < T.nz; k++) {
+          const SZ<R> e = T.s_z[k];
           d += (__popc(e.zm & z[v]) & 1) ? -e.c : e.c;
         }
         const C2 pv = s_p[jm[v]];
@@ -355,15 +386,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
       ai[v] += qv[v].y;
     }
     // 5. epilogue
+    const R h = T.h;
     const R h24 = h / (R)24;
 #pragma unroll
     for (int v = 0; v < kV; v++) {
       if (!ok[v]) continue;
       const uint32_t zz = z[v];
       if (MODE == MODE_PARTIAL) {
-        reinterpret_cast<C2*>(P.qout)[zz] = C2{ar[v], ai[v]};
+        T.qout[zz] = C2{ar[v], ai[v]};
       } else if (MODE == MODE_DERIV) {
-        reinterpret_cast<C2*>(P.fout)[zz] = C2{ai[v], -ar[v]};  // -i (ar + i ai)
+        T.fout[zz] = C2{ai[v], -ar[v]};  // -i (ar + i ai)
       } else if (MODE == MODE_ENERGY) {
         const C2 pv = s_p[jm[v]];
         rt0 += pv.x * ar[v] + pv.y * ai[v];
@@ -376,44 +408,72 @@ __global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
         yn.y = y0[v].y + h24 * ((R)9 * fn.y + (R)19 * a[v].y - (R)5 * b[v].y + c[v].y);
         pn.x = yn.x + h24 * ((R)55 * fn.x - (R)59 * a[v].x + (R)37 * b[v].x - (R)9 * c[v].x);
         pn.y = yn.y + h24 * ((R)55 * fn.y - (R)59 * a[v].y + (R)37 * b[v].y - (R)9 * c[v].y);
-        reinterpret_cast<C2*>(P.y)[zz] = yn;
-        reinterpret_cast<C2*>(P.fout)[zz] = fn;
-        reinterpret_cast<C2*>(P.pout)[zz] = pn;
+        T.y[zz] = yn;
+        T.fout[zz] = fn;
+        T.pout[zz] = pn;
         const C2 pv = s_p[jm[v]];
         const R dx = yn.x - pv.x, dy = yn.y - pv.y;
         rt0 += yn.x * yn.x + yn.y * yn.y;
         rt1 += dx * dx + dy * dy;
       } else if (MODE == MODE_RK4) {
         const C2 k = C2{ai[v], -ar[v]};
-        if (P.stage == 1) {
-          reinterpret_cast<C2*>(P.fout)[zz] = k;
-          reinterpret_cast<C2*>(P.acc)[zz] = k;
+        if (T.stage == 1) {
+          T.fout[zz] = k;
+          T.acc[zz] = k;
           const R hh = (R)0.5 * h;
-          reinterpret_cast<C2*>(P.pout)[zz] = C2{y0[v].x + hh * k.x, y0[v].y + hh * k.y};
-        } else if (P.stage == 2 || P.stage == 3) {
+          T.pout[zz] = C2{y0[v].x + hh * k.x, y0[v].y + hh * k.y};
+        } else if (T.stage == 2 || T.stage == 3) {
           C2 s2 = a[v];
           s2.x += (R)2 * k.x;
           s2.y += (R)2 * k.y;
-          reinterpret_cast<C2*>(P.acc)[zz] = s2;
-          const R hh = P.stage == 2 ? (R)0.5 * h : h;
-          reinterpret_cast<C2*>(P.pout)[zz] = C2{y0[v].x + hh * k.x, y0[v].y + hh * k.y};
+          T.acc[zz] = s2;
+          const R hh = T.stage == 2 ? (R)0.5 * h : h;
+          T.pout[zz] = C2{y0[v].x + hh * k.x, y0[v].y + hh * k.y};
         } else {
           C2 s2 = a[v];
           s2.x += k.x;
           s2.y += k.y;
           const R h6 = h / (R)6;
-          reinterpret_cast<C2*>(P.y)[zz] = C2{y0[v].x + h6 * s2.x, y0[v].y + h6 * s2.y};
+          T.y[zz] = C2{y0[v].x + h6 * s2.x, y0[v].y + h6 * s2.y};
         }
       }
     }
   }
+}
 
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
+  using C2 = typename Cplx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  TileCtx<R> T;
+  load_coefficients<R>(T, P.tab, P.L, P.layout_index, P.with_diag != 0, P.with_remote != 0, P.dcode, P.w[0], P.w[1],
+                       P.w[2], smem);
+  T.stage = P.stage;
+  T.h = (R)P.h;
+  T.src = reinterpret_cast<const C2*>(P.src);
+  T.qin = reinterpret_cast<const C2*>(P.qin);
+  T.qout = reinterpret_cast<C2*>(P.qout);
+  T.y = reinterpret_cast<C2*>(P.y);
+  T.f0 = reinterpret_cast<const C2*>(P.f0);
+  T.f1 = reinterpret_cast<const C2*>(P.f1);
+  T.f2 = reinterpret_cast<const C2*>(P.f2);
+  T.fout = reinterpret_cast<C2*>(P.fout);
+  T.pout = reinterpret_cast<C2*>(P.pout);
+  T.acc = reinterpret_cast<C2*>(P.acc);
+
+  // reductions: per-thread partials over one tile in the state precision (a few dozen
+  // points), promoted to FP64 once per tile; FP64 across tiles, CTAs and the grid
+  double red[2] = {0.0, 0.0};
+  // persistent CTAs: one prologue and one reduction per CTA, tiles taken round-robin
+  for (uint32_t tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
+    R rt0 = (R)0, rt1 = (R)0;
+    process_tile<R, MODE>(T, tile, rt0, rt1);
     red[0] += (double)rt0;
     red[1] += (double)rt1;
-  }  // tile loop
+  }
 
   if (MODE == MODE_STEP || MODE == MODE_ENERGY) {
-    if (grid_reduce<2>(red, P.partials, P.counter, s_red)) {
+    if (grid_reduce<2>(red, P.partials, P.counter, T.s_red)) {
       if (MODE == MODE_STEP) {
         P.slots[kSlotNorm2] = red[0];
         const double e = (19.0 / 270.0) * sqrt(red[1]);
@@ -424,6 +484,81 @@ __global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
         P.slots[kSlotDotIm] = red[1];
       }
     }
+  }
+}
+
+// ---- batched stepping -----------------------------------------------------------------
+// Schedule weights on the device (same expression as the host side).
+__device__ __forceinline__ double batch_weight(const BatchInst& I, double s, int g) {
+  return ((I.poly[g][3] * s + I.poly[g][2]) * s + I.poly[g][1]) * s + I.poly[g][0];
+}
+
+// One PEC grid step of many independent states per launch.  Each CTA takes one work item
+// (member, tile) of layout level `level`; a member whose integration is finished is skipped.
+// Level > 0: partial sums into the member's q; level 0: the fused PEC step (as k_apply
+// MODE_STEP), with per-member reductions summed by the member's last CTA, which then advances
+// the member's step counter.
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) k_batch(BatchLaunch B) {
+  using C2 = typename Cplx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BatchItem it = B.items[blockIdx.x];
+  BatchInst* I = B.insts + it.inst;
+  const int64_t n = I->step;
+  if (n >= I->nsteps) return;  // finished member: uniform for the whole CTA
+  const int level = B.level;
+  const int nl = I->nl;
+  const double tau = (double)(n + 1) * I->h / I->T;
+  const double s = I->s_kind == 1 ? tau * tau * (3.0 - 2.0 * tau) : tau;
+  TileCtx<R> T;
+  const bool first = (level == nl - 1);  // first layout pass of this member's evaluation
+  load_coefficients<R>(T, I->tab, I->layouts[level], level, first, first, I->dcode, batch_weight(*I, s, 0),
+                       batch_weight(*I, s, 1), batch_weight(*I, s, 2), smem);
+  T.stage = 0;
+  T.h = (R)I->h;
+  C2* const* v = reinterpret_cast<C2* const*>(I->vec);
+  T.src = v[kVecP];
+  T.qin = first ? nullptr : v[kVecQ];
+  T.qout = v[kVecQ];
+  T.y = v[kVecY];
+  T.f0 = v[kVecF0 + (int)(n & 3)];
+  T.f1 = v[kVecF0 + (int)((n - 1) & 3)];
+  T.f2 = v[kVecF0 + (int)((n - 2) & 3)];
+  T.fout = v[kVecF0 + (int)((n + 1) & 3)];
+  T.pout = v[kVecP];
+  T.acc = nullptr;
+  R rt0 = (R)0, rt1 = (R)0;
+  if (level > 0) {
+    process_tile<R, MODE_PARTIAL>(T, it.tile, rt0, rt1);
+    return;
+  }
+  process_tile<R, MODE_STEP>(T, it.tile, rt0, rt1);
+  double red[2] = {(double)rt0, (double)rt1};
+  cta_reduce<2>(red, T.s_red);
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    B.partials[2 * (size_t)blockIdx.x] = red[0];
+    B.partials[2 * (size_t)blockIdx.x + 1] = red[1];
+    __threadfence();
+    const unsigned ticket = atomicAdd(&I->ticket, 1u);
+    s_last = (ticket == I->item_end - I->item_begin - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double acc[2] = {0.0, 0.0};
+  for (uint32_t k = I->item_begin + threadIdx.x; k < I->item_end; k += blockDim.x) {
+    acc[0] += __ldcg(&B.partials[2 * (size_t)k]);
+    acc[1] += __ldcg(&B.partials[2 * (size_t)k + 1]);
+  }
+  cta_reduce<2>(acc, T.s_red);
+  if (threadIdx.x == 0) {
+    I->norm2 = acc[0];
+    const double e = (19.0 / 270.0) * sqrt(acc[1]);
+    I->last_err = e;
+    if (!(e <= I->max_err)) I->max_err = e;
+    I->ticket = 0u;
+    I->step = n + 1;
   }
 }
 
@@ -486,6 +621,26 @@ static cudaError_t launch_prec(const ApplyParams& p, int smem, cudaStream_t s) {
 
 cudaError_t launch_apply(int prec, const ApplyParams& p, int smem, cudaStream_t s) {
   return prec == 0 ? launch_prec<double>(p, smem, s) : launch_prec<float>(p, smem, s);
+}
+
+template <typename R, int NT>
+static cudaError_t launch_batch_t(const BatchLaunch& b, int nitems, int smem, cudaStream_t s) {
+  static int configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_batch<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  k_batch<R, NT><<<nitems, NT, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch(int prec, int threads, const BatchLaunch& b, int nitems, int smem, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (prec == 0) {
+    return threads == 128 ? launch_batch_t<double, 128>(b, nitems, smem, s) : launch_batch_t<double, 256>(b, nitems, smem, s);
+  }
+  return threads == 128 ? launch_batch_t<float, 128>(b, nitems, smem, s) : launch_batch_t<float, 256>(b, nitems, smem, s);
 }
 
 // per-index clause counts of one class (computed once per Hamiltonian)

@@ -146,3 +146,78 @@ class Context:
             out = torch.empty_like(psi)
         N.aqc_hpsi(self.handle, t, psi.data_ptr(), out.data_ptr())
         return out
+
+
+class Batch:
+    """Many contexts stepped together (include/aqc.h, aqc_batch_*): batched PEC launches over
+    (member, tile) work items, K steps per CUDA-graph replay."""
+
+    def __init__(self, precision=N.AQC_C64, device=0, max_members=64, max_items=1 << 16, stream=None,
+                 threads=256, steps_per_round=16):
+        self.precision = precision
+        self.device = device
+        self.dev = torch.device("cuda", device)
+        self.max_members = max_members
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.dev)
+        self.ws_bytes = N.aqc_batch_workspace_bytes(max_members, max_items)
+        if self.ws_bytes == 0:
+            raise ValueError("unsupported batch size")
+        self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.dev)
+        ptr = (self.workspace.data_ptr() + 255) // 256 * 256
+        self.handle = N.aqc_batch_create(device, precision, max_members, max_items, ptr, self.ws_bytes,
+                                         self.stream.cuda_stream)
+        self.members = {}
+        N.aqc_batch_set_shape(self.handle, threads, steps_per_round)
+        self.threads = threads
+        self.steps_per_round = steps_per_round
+
+    def set_shape(self, threads, steps_per_round):
+        N.aqc_batch_set_shape(self.handle, threads, steps_per_round)
+        self.threads = threads
+        self.steps_per_round = steps_per_round
+
+    def add(self, ctx: Context) -> int:
+        slot = N.aqc_batch_add(self.handle, ctx.handle)
+        self.members[slot] = ctx
+        return slot
+
+    def remove(self, slot) -> Context:
+        N.aqc_batch_remove(self.handle, slot)
+        return self.members.pop(slot)
+
+    def run(self, rounds=1):
+        N.aqc_batch_run(self.handle, rounds)
+
+    def poll(self):
+        steps, active, launches = N.aqc_batch_poll(self.handle, self.max_members)
+        return steps, active, launches
+
+    def run_to_completion(self, rounds_per_poll=8, max_polls=1 << 30):
+        """Replay rounds until every member reached its t = T; returns the number of polls."""
+        polls = 0
+        while polls < max_polls:
+            self.run(rounds_per_poll)
+            _, active, _ = self.poll()
+            polls += 1
+            if active == 0:
+                break
+        return polls
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.stream.synchronize()
+            N.aqc_batch_destroy(self.handle)
+            self.handle = None
+            self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
