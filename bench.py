@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--no-c128", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=48)
+    ap.add_argument("--serve-count", type=int, default=40)
     return ap.parse_args()
 
 
@@ -171,6 +175,56 @@ def cpu_sample(target_s=15.0):
     return gbs, cores, desc, dt
 
 
+# ----------------------------------------------------------------------------- batch / serve
+def measure_batched(a):
+    """Batched vs one-at-a-time solves on a sample of the 512-instance batched workload
+    (seeds from 1000, n ~ U{12..18}, nonlinear path, T ~ U[10, 40], complex64): same step
+    grids, so equal final-fidelity accuracy by construction (checked)."""
+    import copy
+
+    from paper_1311_3938_gb300 import autotune as A
+    from paper_1311_3938_gb300 import workloads as W
+
+    jobs = W.random_jobs(a.batch_count, 1000, n_range=(12, 18), T_range=(10.0, 40.0), nonlinear=True)
+    shape, tune = A.autotune(jobs[: min(16, len(jobs))], rounds=3)
+    tile_bits, threads, spr = shape
+    jb = copy.deepcopy(jobs)
+    t_batch = W.run_batched(jb, threads=threads, steps_per_round=spr, tile_bits=tile_bits)
+    js = copy.deepcopy(jobs)
+    t_seq = W.run_sequential(js)
+    dP1 = max(abs(x.P1 - y.P1) for x, y in zip(jb, js))
+    steps = sum(j.steps for j in jb)
+    return {
+        "workload": f"{len(jobs)} EC3 instances, seeds 1000-{999 + len(jobs)}, n~U{{12..18}}, nonlinear, "
+                    "T~U[10,40], complex64 (sample of the 512-instance n~U{12..22} T~U[10,200] workload)",
+        "solves_per_s_batched": len(jobs) / t_batch,
+        "solves_per_s_sequential": len(jobs) / t_seq,
+        "speedup": t_seq / t_batch,
+        "grid_steps_total": steps,
+        "max_abs_dP1_batched_vs_sequential": dP1,
+        "autotuned_shape": {"tile_bits": tile_bits, "threads": threads, "steps_per_round": spr},
+    }
+
+
+def measure_serving(a):
+    """Continuous batching of a seeded Poisson stream (rate 8/s): n ~ U{10..20} with every
+    20th job n = 30 (64 GiB workspace), linear/nonlinear uniform, T ~ U[2, 20] (n = 30:
+    T ~ U[0.1, 0.3]), complex64, admission by HBM budget (free memory - 2 GiB)."""
+    from paper_1311_3938_gb300 import workloads as W
+
+    jobs = W.random_jobs(a.serve_count, 2000, n_range=(10, 20), T_range=(2.0, 20.0), rate=8.0, big_every=20,
+                         big_n=30, path_mix=True, big_T_range=(0.1, 0.3))
+    srv = W.Server(batch_max_n=20, max_members=128, steps_per_round=16, big_chunk=32)
+    try:
+        res = srv.serve(jobs)
+    finally:
+        srv.close()
+    res.pop("jobs")
+    res["workload"] = (f"{len(jobs)} requests, Poisson rate 8/s, n~U{{10..20}} + every 20th n=30, "
+                       "path linear/nonlinear, T~U[2,20] (n=30: U[0.1,0.3]), complex64")
+    return res
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(a):
     import numpy as np
@@ -296,6 +350,8 @@ def run_ours(a):
 
     r64 = measure(P.AQC_C64)
     r128 = None if a.no_c128 else measure(P.AQC_C128)
+    batched = None if a.no_batch else measure_batched(a)
+    serving = None if a.no_serve else measure_serving(a)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         gbs, cores, desc, _ = cpu_sample()
@@ -344,6 +400,8 @@ def run_ours(a):
         "gpu_launches": r64["launches"],
         "clocks": r64["clocks"],
         "fidelity_P1_window": r64["P1"],
+        "batched": batched,
+        "serving": serving,
     }
     if r128 is not None:
         flops = pec_flops_c128(n) * (1 << n)

@@ -130,6 +130,14 @@ int aqc_set_schedule(aqc_ctx *ctx, int s_kind, double T, const double coefA[4], 
  * (0 selects 0.1; the PEC scheme is stable on the imaginary axis up to about 0.22). */
 int aqc_set_integrator(aqc_ctx *ctx, int64_t n_steps, double kappa);
 
+/* The step grid the next (or current) propagation uses: N and h = T/N (step rule above). */
+int aqc_get_grid(aqc_ctx *ctx, int64_t *n_steps, double *h);
+
+/* Tile size of the shared-memory tiles (2^tile_bits amplitudes per CTA tile; 0 = default:
+ * 13 for AQC_C64, 12 for AQC_C128; allowed 6..13 / 5..12).  Smaller tiles give more CTAs for
+ * small states but more layout passes for large ones.  Resets the integrator. */
+int aqc_set_tile_bits(aqc_ctx *ctx, int tile_bits);
+
 /* Set psi(0) and reset the integrator to t = 0.  kind = AQC_INIT_*; `basis` for
  * AQC_INIT_BASIS; `user` points to 2^n interleaved amplitudes in the state precision. */
 int aqc_set_initial_state(aqc_ctx *ctx, int kind, uint64_t basis, const void *user);

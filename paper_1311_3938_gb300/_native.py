@@ -74,6 +74,8 @@ def lib():
             "aqc_clear_hamiltonian": (i32, [vp]),
             "aqc_set_schedule": (i32, [vp, i32, dbl, vp, vp, vp]),
             "aqc_set_integrator": (i32, [vp, i64, dbl]),
+            "aqc_set_tile_bits": (i32, [vp, i32]),
+            "aqc_get_grid": (i32, [vp, C.POINTER(i64), C.POINTER(dbl)]),
             "aqc_set_initial_state": (i32, [vp, i32, u64, vp]),
             "aqc_propagate": (i32, [vp, i64, C.POINTER(aqc_stats)]),
             "aqc_get_state": (i32, [vp, vp, i32]),
@@ -157,6 +159,17 @@ def aqc_set_schedule(ctx, s_kind, T, coefA, coefB, coefC):
 
 def aqc_set_integrator(ctx, n_steps, kappa):
     _check(ctx, lib().aqc_set_integrator(ctx, int(n_steps), float(kappa)))
+
+
+def aqc_get_grid(ctx):
+    n = C.c_int64()
+    h = C.c_double()
+    _check(ctx, lib().aqc_get_grid(ctx, C.byref(n), C.byref(h)))
+    return n.value, h.value
+
+
+def aqc_set_tile_bits(ctx, tile_bits):
+    _check(ctx, lib().aqc_set_tile_bits(ctx, int(tile_bits)))
 
 
 def aqc_set_initial_state(ctx, kind, basis, user_ptr):

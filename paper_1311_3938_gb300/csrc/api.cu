@@ -36,9 +36,9 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int tile_bits_max(int prec) { return prec == AQC_C128 ? 12 : 13; }
 int chunk_bits(int prec) { return prec == AQC_C128 ? 4 : 5; }  // 256-byte contiguous chunks
 
-std::vector<Layout> layouts_for(int n, int prec) {
+std::vector<Layout> layouts_for(int n, int prec, int tile_bits) {
   std::vector<Layout> ls;
-  const int tmax = tile_bits_max(prec), cc = chunk_bits(prec);
+  const int tmax = tile_bits > 0 ? tile_bits : tile_bits_max(prec), cc = chunk_bits(prec);
   if (n <= tmax) {
     ls.push_back(Layout{n, n, 0, n});
     return ls;
@@ -55,11 +55,6 @@ std::vector<Layout> layouts_for(int n, int prec) {
   return ls;
 }
 
-size_t max_tiles(int n, int prec) {
-  size_t g = 1;
-  for (const Layout& L : layouts_for(n, prec)) g = std::max(g, (size_t)1 << (n - L.t));
-  return g;
-}
 
 struct WsPlan {
   size_t off_tab, off_slots, off_counter, off_partials, off_dcode, off_vec, vec_bytes, total;
@@ -73,7 +68,8 @@ WsPlan plan_workspace(int n, int prec) {
   w.off_slots = align_up(sizeof(DevTables), 256);
   w.off_counter = w.off_slots + 256;
   w.off_partials = w.off_counter + 256;
-  size_t g = std::max(max_tiles(n, prec), (size_t)reduce_grid((uint64_t)1 << n));
+  // k_apply grids are persistent (at most kMaxApplyGrid CTAs); k_norm2 uses reduce_grid()
+  size_t g = std::max((size_t)kMaxApplyGrid, (size_t)reduce_grid((uint64_t)1 << n));
   w.partial_doubles = 3 * g;
   w.off_dcode = align_up(w.off_partials + w.partial_doubles * sizeof(double), 256);
   w.off_vec = align_up(w.off_dcode + ((size_t)1 << n), 256);
@@ -115,6 +111,7 @@ struct aqc_ctx {
   double poly[3][4];
   int64_t nsteps_req = 0;
   double kappa = 0.1;
+  int tile_bits = 0;  // 0: the precision's default
 
   bool have_state = false;
   bool hist_ready = false;
@@ -171,7 +168,7 @@ uint32_t compress_mask(const Layout& L, uint32_t x) {
   return r;
 }
 
-void plan_layouts(aqc_ctx* c) { c->layouts = layouts_for(c->n, c->prec); }
+void plan_layouts(aqc_ctx* c) { c->layouts = layouts_for(c->n, c->prec, c->tile_bits); }
 
 int build_tables(aqc_ctx* c) {
   plan_layouts(c);
@@ -744,6 +741,17 @@ int aqc_set_schedule(aqc_ctx* ctx, int s_kind, double T, const double coefA[4], 
   return AQC_OK;
 }
 
+int aqc_set_tile_bits(aqc_ctx* ctx, int tile_bits) {
+  if (!ctx) return AQC_E_INVAL;
+  const int lo = chunk_bits(ctx->prec) + 1, hi = tile_bits_max(ctx->prec);
+  if (tile_bits != 0 && (tile_bits < lo || tile_bits > hi))
+    FAIL(ctx, AQC_E_INVAL, "tile_bits must be 0 or in [%d, %d]", lo, hi);
+  ctx->tile_bits = tile_bits;
+  ctx->dirty = true;
+  ctx->have_state = false;
+  return AQC_OK;
+}
+
 int aqc_set_integrator(aqc_ctx* ctx, int64_t n_steps, double kappa) {
   if (!ctx) return AQC_E_INVAL;
   if (n_steps < 0) FAIL(ctx, AQC_E_INVAL, "n_steps must be >= 0");
@@ -751,6 +759,15 @@ int aqc_set_integrator(aqc_ctx* ctx, int64_t n_steps, double kappa) {
   ctx->nsteps_req = n_steps;
   ctx->kappa = kappa > 0.0 ? kappa : 0.1;
   ctx->have_state = false;
+  return AQC_OK;
+}
+
+int aqc_get_grid(aqc_ctx* ctx, int64_t* n_steps, double* h) {
+  if (!ctx) return AQC_E_INVAL;
+  if (!ctx->have_sched) FAIL(ctx, AQC_E_STATE, "no schedule set");
+  const int64_t N = ctx->nsteps > 0 ? ctx->nsteps : (ctx->nsteps_req > 0 ? ctx->nsteps_req : rule_steps(ctx));
+  if (n_steps) *n_steps = N;
+  if (h) *h = ctx->T / (double)N;
   return AQC_OK;
 }
 

@@ -11,6 +11,7 @@ constexpr int kMaxClauses = 1024; // EC3 clauses
 constexpr int kMaxClasses = 8;    // (group, penalty kind, scale) classes of clauses
 constexpr int kMaxLayouts = 8;
 constexpr int kMaxN = 31;
+constexpr int kMaxApplyGrid = 4096;  // persistent k_apply grids never exceed this many CTAs
 
 // One off-diagonal Pauli product in gather form: (P psi)(z) = i^ipow (-1)^{|zm & (z^x)|} psi(z^x).
 struct DevFlip {

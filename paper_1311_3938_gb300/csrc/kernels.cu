@@ -593,7 +593,8 @@ static cudaError_t grid_for(uint32_t ntiles, int smem, int* grid) {
     cached_per = per;
   }
   if (per < 1) per = 1;
-  const uint64_t g = (uint64_t)sms * (uint64_t)per;
+  uint64_t g = (uint64_t)sms * (uint64_t)per;
+  if (g > (uint64_t)kMaxApplyGrid) g = kMaxApplyGrid;
   *grid = (int)(g < ntiles ? g : ntiles);
   return cudaSuccess;
 }

@@ -82,6 +82,13 @@ class Context:
     def set_schedule(self, T, weights, s_kind=N.AQC_S_LINEAR):
         N.aqc_set_schedule(self.handle, s_kind, T, *weights)
 
+    def grid(self):
+        """(N, h) of the step grid."""
+        return N.aqc_get_grid(self.handle)
+
+    def set_tile_bits(self, tile_bits=0):
+        N.aqc_set_tile_bits(self.handle, tile_bits)
+
     def set_integrator(self, n_steps=0, kappa=0.0):
         N.aqc_set_integrator(self.handle, n_steps, kappa)
 

@@ -1,0 +1,285 @@
+"""Batched solves and a continuous-batching request server on top of the C ABI.
+
+* `Job`: one Exact-Cover-3 solve (instance seed, n, path, T, precision).
+* `solve_single(job)`: the job alone through aqc_propagate (one context, its own stream).
+* `run_batched(jobs, ...)`: all jobs as members of one aqc_batch (K PEC steps per graph
+  replay), members retired as they reach t = T.
+* `Server`: requests arrive over time (Poisson); each is admitted when its workspace fits the
+  HBM budget; small states join the running batch between rounds (continuous batching), large
+  states run on their own streams concurrently with the batch; finished jobs are retired and
+  their memory released.  Reports p50/p99 latency, solves/s and HBM occupancy.
+
+All device work is libaqc.so's; this module only schedules it.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from instances import SplitMix64, generate_ec3, xx_pairs
+
+from . import _native as N
+from . import hamiltonians as HB
+from .engine import Batch, Context
+
+
+@dataclass
+class Job:
+    jid: int
+    n: int
+    seed: int
+    nonlinear: bool
+    T: float
+    precision: int = N.AQC_C64
+    s_kind: int = N.AQC_S_LINEAR
+    arrival: float = 0.0
+    # filled in when the job is served
+    admitted: float = math.nan
+    finished: float = math.nan
+    P1: float = math.nan
+    E: float = math.nan
+    norm2: float = math.nan
+    steps: int = 0
+    route: str = ""
+    state: np.ndarray = field(default=None, repr=False)
+
+    @property
+    def latency(self):
+        return self.finished - self.arrival
+
+    def workspace_bytes(self):
+        return N.aqc_workspace_bytes(self.n, self.precision)
+
+
+_INSTANCE_CACHE = {}
+
+
+def _instance(n, seed):
+    key = (n, seed)
+    if key not in _INSTANCE_CACHE:
+        _INSTANCE_CACHE[key] = generate_ec3(n, seed)
+    return _INSTANCE_CACHE[key]
+
+
+def make_context(job: Job, device=0, stream=None, tile_bits=0) -> tuple:
+    inst = _instance(job.n, job.seed)
+    pairs = xx_pairs(job.n, job.seed) if job.nonlinear else None
+    ctx = Context(job.n, job.precision, device=device, stream=stream)
+    if tile_bits:
+        ctx.set_tile_bits(tile_bits)
+    HB.load_ec3(ctx, inst, pairs=pairs)
+    ctx.set_schedule(job.T, HB.nonlinear_schedule() if job.nonlinear else HB.linear_schedule(), job.s_kind)
+    ctx.set_integrator(0, 0.0)
+    ctx.set_initial_state("uniform")
+    return ctx, inst
+
+
+def _finish(job: Job, ctx: Context, inst, keep_state: bool):
+    job.P1 = ctx.fidelity(inst.solution)
+    job.E = ctx.energy(N.AQC_GRP_B)
+    job.norm2 = ctx.norm2()
+    if keep_state:
+        job.state = ctx.state()
+
+
+def solve_single(job: Job, device=0, keep_state=False, stream=None) -> Job:
+    """The job alone: one context, aqc_propagate to t = T."""
+    ctx, inst = make_context(job, device, stream)
+    st = ctx.propagate(-1)
+    job.steps = st["steps_done"]
+    job.route = "single"
+    _finish(job, ctx, inst, keep_state)
+    ctx.close()
+    return job
+
+
+def random_jobs(count, seed, n_range=(12, 22), T_range=(10.0, 200.0), nonlinear=True, precision=N.AQC_C64,
+                rate=None, big_every=0, big_n=30, s_kind=N.AQC_S_LINEAR, path_mix=False, big_T_range=None):
+    """Seeded job list: n ~ U{n_range}, T ~ U[T_range], instance seeds seed..seed+count-1;
+    with `rate`, Poisson arrival times (exponential gaps of mean 1/rate seconds); every
+    `big_every`-th job has n = big_n (and T ~ U[big_T_range] if given); `path_mix` draws
+    linear/nonlinear uniformly."""
+    rng = SplitMix64(seed * 7919 + 17)
+    jobs = []
+    t = 0.0
+    for k in range(count):
+        n = n_range[0] + rng.below(n_range[1] - n_range[0] + 1)
+        T = T_range[0] + (T_range[1] - T_range[0]) * rng.uniform()
+        if big_every and (k + 1) % big_every == 0:
+            n = big_n
+            if big_T_range:
+                T = big_T_range[0] + (big_T_range[1] - big_T_range[0]) * (T - T_range[0]) / max(1e-300, T_range[1] - T_range[0])
+        nl = (rng.below(2) == 1) if path_mix else nonlinear
+        if rate:
+            t += -math.log(1.0 - rng.uniform()) / rate
+        jobs.append(Job(jid=k, n=n, seed=seed + k, nonlinear=nl, T=T, precision=precision, s_kind=s_kind, arrival=t))
+    return jobs
+
+
+def run_batched(jobs, device=0, threads=256, steps_per_round=16, rounds_per_poll=4, keep_state=False,
+                tile_bits=0, max_members=None):
+    """Every job a member of one batch; members retire at t = T.  Returns wall seconds."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mm = max_members or len(jobs)
+    items = 1
+    for j in jobs:
+        items += 1 << max(0, j.n - (tile_bits or (13 if j.precision == N.AQC_C64 else 12)) + 3)
+    b = Batch(jobs[0].precision, device=device, max_members=mm, max_items=max(items, 1024), threads=threads,
+              steps_per_round=steps_per_round)
+    live = {}
+    queue = list(jobs)
+    while queue or live:
+        while queue and len(live) < mm:
+            job = queue.pop(0)
+            ctx, inst = make_context(job, device, tile_bits=tile_bits)
+            slot = b.add(ctx)
+            live[slot] = (job, ctx, inst)
+        b.run(rounds_per_poll)
+        steps, active, _ = b.poll()
+        for slot in list(live):
+            job, ctx, inst = live[slot]
+            if steps[slot] >= 0 and b.members.get(slot) is ctx and steps[slot] >= _nsteps(ctx, job):
+                b.remove(slot)
+                job.steps = steps[slot]
+                job.route = "batch"
+                _finish(job, ctx, inst, keep_state)
+                ctx.close()
+                del live[slot]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    b.close()
+    return dt
+
+
+def _nsteps(ctx, job):
+    """N of the context's step grid (asked once from the library)."""
+    if getattr(ctx, "_nsteps", None) is None:
+        ctx._nsteps = ctx.grid()[0]
+    return ctx._nsteps
+
+
+def run_sequential(jobs, device=0, keep_state=False):
+    """Every job alone, one after another (the one-at-a-time baseline).  Returns wall seconds."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for job in jobs:
+        solve_single(job, device, keep_state)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0
+
+
+class Server:
+    """Continuous-batching request loop (see the module docstring)."""
+
+    def __init__(self, precision=N.AQC_C64, device=0, hbm_budget=None, reserve=2 << 30, batch_max_n=22,
+                 max_members=256, threads=256, steps_per_round=16, big_chunk=64, keep_state=False):
+        self.precision = precision
+        self.device = device
+        free, total = torch.cuda.mem_get_info(device)
+        self.budget = int(hbm_budget if hbm_budget is not None else free - reserve)
+        self.batch_max_n = batch_max_n
+        self.max_members = max_members
+        self.big_chunk = big_chunk
+        self.keep_state = keep_state
+        max_items = max_members * (1 << max(0, batch_max_n - 13 + 2)) + 1024
+        self.batch = Batch(precision, device=device, max_members=max_members, max_items=max_items, threads=threads,
+                           steps_per_round=steps_per_round)
+        self.used = 0
+        self.peak_used = 0
+        self.occupancy = []
+
+    def serve(self, jobs, time_limit=None):
+        """Serve `jobs` (arrival times in seconds from now).  Returns a metrics dict."""
+        pending = sorted(jobs, key=lambda j: j.arrival)
+        in_batch = {}  # slot -> (job, ctx, inst)
+        big = []  # [job, ctx, inst, stream, event, steps_enqueued]
+        done = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0  # noqa: E731
+        while pending or in_batch or big:
+            if time_limit and now() > time_limit:
+                break
+            # admission: FIFO among arrived jobs, as memory allows
+            while pending and pending[0].arrival <= now():
+                job = pending[0]
+                need = job.workspace_bytes()
+                small = job.n <= self.batch_max_n
+                if self.used + need > self.budget or (small and len(in_batch) >= self.max_members):
+                    break
+                pending.pop(0)
+                job.admitted = now()
+                self.used += need
+                self.peak_used = max(self.peak_used, self.used)
+                if small:
+                    ctx, inst = make_context(job, self.device)
+                    slot = self.batch.add(ctx)
+                    in_batch[slot] = (job, ctx, inst)
+                else:
+                    stream = torch.cuda.Stream(self.device)
+                    ctx, inst = make_context(job, self.device, stream=stream)
+                    big.append([job, ctx, inst, stream, None, 0])
+            self.occupancy.append(self.used / max(1, self.budget))
+            if not in_batch and not big:
+                if pending:
+                    time.sleep(min(0.01, max(0.0, pending[0].arrival - now())))
+                continue
+            # advance: one batch round and one chunk per large job, on different streams
+            if in_batch:
+                self.batch.run(1)
+            for entry in big:
+                job, ctx, inst, stream, ev, enq = entry
+                if ev is None:
+                    with torch.cuda.stream(stream):
+                        ctx.propagate(self.big_chunk, stats=False)
+                    entry[5] = enq + self.big_chunk
+                    if entry[5] >= _nsteps(ctx, job):
+                        entry[4] = torch.cuda.Event()
+                        entry[4].record(stream)
+            # retire finished work
+            if in_batch:
+                steps, _, _ = self.batch.poll()
+                for slot in list(in_batch):
+                    job, ctx, inst = in_batch[slot]
+                    if steps[slot] >= _nsteps(ctx, job):
+                        self.batch.remove(slot)
+                        job.steps = steps[slot]
+                        job.route = "batch"
+                        _finish(job, ctx, inst, self.keep_state)
+                        job.finished = now()
+                        ctx.close()
+                        self.used -= job.workspace_bytes()
+                        del in_batch[slot]
+                        done.append(job)
+            for entry in list(big):
+                job, ctx, inst, stream, ev, enq = entry
+                if ev is not None and ev.query():
+                    job.steps = _nsteps(ctx, job)
+                    job.route = "stream"
+                    _finish(job, ctx, inst, self.keep_state)
+                    job.finished = now()
+                    ctx.close()
+                    self.used -= job.workspace_bytes()
+                    big.remove(entry)
+                    done.append(job)
+        wall = now()
+        lat = np.array([j.latency for j in done]) if done else np.array([math.nan])
+        return {
+            "completed": len(done),
+            "wall_s": wall,
+            "solves_per_s": len(done) / wall if wall > 0 else math.nan,
+            "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "hbm_budget_bytes": self.budget,
+            "hbm_peak_bytes": self.peak_used,
+            "hbm_mean_occupancy": float(np.mean(self.occupancy)) if self.occupancy else 0.0,
+            "jobs": done,
+        }
+
+    def close(self):
+        self.batch.close()
