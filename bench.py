@@ -146,6 +146,33 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# ----------------------------------------------------------------------------- replicas
+def replica_barrier(dist, device):
+    """Barrier across replicas (no-op for one process)."""
+    if dist is not None:
+        if device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def replica_max(dist, x, device):
+    """Max of a scalar over replicas: the job's time is its slowest replica's."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(bytes_per_step, steps, world, ms_max):
+    """Whole-job throughput: every replica processes its own copy of the workload (weak
+    scaling), the job ends with the slowest replica."""
+    return bytes_per_step * steps * world / (ms_max * 1e-3) / 1e9
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 def cpu_sample(target_s=15.0):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload: the same EC3
@@ -248,17 +275,13 @@ def run_ours(a):
     n = a.n
     inst = generate_ec3(n, SEED)
     hbm_peak, peak_kind = peaks()
+    dev = torch.device("cuda", local)
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        replica_barrier(dist, dev)
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(dist, x, dev)
 
     def measure(prec):
         amp = 16 if prec == P.AQC_C128 else 8
@@ -300,7 +323,7 @@ def run_ours(a):
         ms = e0.elapsed_time(e1)
         ms = max_over_ranks(ms)
         ab = alg_bytes(n, amp, a.pec)
-        value = ab * a.steps * world / (ms * 1e-3) / 1e9
+        value = whole_job_value(ab, a.steps, world, ms)
         pec_step_ms = statistics.mean(pec_ms)
         pec_ach = 7 * (1 << n) * amp / (pec_step_ms * 1e-3) / 1e9
         out = {
@@ -337,7 +360,7 @@ def run_ours(a):
             torch.cuda.synchronize()
             dt = max_over_ranks(time.perf_counter() - t0)
             out["e2e"] = {
-                "value": ab * a.steps * world / dt / 1e9,
+                "value": whole_job_value(ab, a.steps, world, dt * 1e3),
                 "unit": "GB/s",
                 "h2d_bytes_per_step": (1 << n) * amp,
                 "d2h_bytes_per_step": (1 << n) * amp + 16,
@@ -350,8 +373,8 @@ def run_ours(a):
 
     r64 = measure(P.AQC_C64)
     r128 = None if a.no_c128 else measure(P.AQC_C128)
-    batched = None if a.no_batch else measure_batched(a)
-    serving = None if a.no_serve else measure_serving(a)
+    batched = None if (a.no_batch or world > 1) else measure_batched(a)
+    serving = None if (a.no_serve or world > 1) else measure_serving(a)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         gbs, cores, desc, _ = cpu_sample()

@@ -166,6 +166,45 @@ int or_hpsi(const or_ham *H, const double w[3], const double *psi, double *out, 
   return 0;
 }
 
+/* Selected outputs (H psi)(z) for z in zs[0..nz): for every stored product, the one basis state
+ * z' whose image under the product is |z> (z' = z xor xmask) contributes coef * (the product's
+ * matrix element <z|P|z'>) * psi[z'], the element being built qubit by qubit as in the scatter
+ * loop; clause penalties add their diagonal value at z.  Used to check single outputs of very
+ * large states. */
+int or_hpsi_at(const or_ham *H, const double w[3], const double *psi, int64_t nz, const uint64_t *zs, double *out) {
+  for (int64_t k = 0; k < nz; k++) {
+    const uint64_t z = zs[k];
+    double acc_re = 0.0, acc_im = 0.0;
+    for (int t = 0; t < H->nterms; t++) {
+      double c = w[H->term_group[t]] * H->coef[t];
+      if (c == 0.0) continue;
+      uint64_t zsrc = z ^ H->xmask[t];
+      double re = psi[2 * zsrc], im = psi[2 * zsrc + 1];
+      uint64_t zimg = zsrc;
+      for (int q = 0; q < H->n; q++) {
+        int xq = (int)((H->xmask[t] >> q) & 1u);
+        int zq = (int)((H->zmask[t] >> q) & 1u);
+        if (!xq && !zq) continue;
+        int b = (int)((zsrc >> q) & 1u);
+        int nb = pauli_on_bit(xq, zq, b, &re, &im);
+        zimg = (zimg & ~(1ull << q)) | ((uint64_t)nb << q);
+      }
+      if (zimg != z) return -3; /* cannot happen: the image of z^x under P is z */
+      acc_re += c * re;
+      acc_im += c * im;
+    }
+    double d = 0.0;
+    for (int j = 0; j < H->nclauses; j++) {
+      const int *cb = H->clause_bits + 3 * j;
+      int ones = (int)((z >> cb[0]) & 1u) + (int)((z >> cb[1]) & 1u) + (int)((z >> cb[2]) & 1u);
+      d += w[H->clause_group[j]] * H->clause_scale[j] * clause_penalty(H->clause_penalty[j], ones);
+    }
+    out[2 * k] = acc_re + d * psi[2 * z];
+    out[2 * k + 1] = acc_im + d * psi[2 * z + 1];
+  }
+  return 0;
+}
+
 /* f = -i H(t) y   (Eq. schroedinger with hbar = 1) */
 static int deriv(const or_ham *H, const or_sched *sc, double t, const double *y, double *f, double *tmp,
                  uint64_t N, int nthreads) {

@@ -88,6 +88,9 @@ def _load():
         lib.or_propagate.argtypes = [C.POINTER(_Ham), C.POINTER(_Sched), C.c_int64, C.c_int64, C.c_void_p,
                                      C.POINTER(_Stats), C.c_int]
         lib.or_propagate.restype = C.c_int
+        lib.or_hpsi_at.argtypes = [C.POINTER(_Ham), C.POINTER(C.c_double), C.c_void_p, C.c_int64, C.c_void_p,
+                                   C.c_void_p]
+        lib.or_hpsi_at.restype = C.c_int
         lib.or_weights.argtypes = [C.POINTER(_Sched), C.c_double, C.POINTER(C.c_double)]
         lib.or_weights.restype = None
         _lib = lib
@@ -252,6 +255,22 @@ def hpsi(H: Hamiltonian, weights, psi, nthreads=1):
     rc = lib.or_hpsi(C.byref(h), w, psi.ctypes.data, out.ctypes.data, int(nthreads))
     if rc != 0:
         raise RuntimeError("or_hpsi failed")
+    return out
+
+
+def hpsi_at(H: Hamiltonian, weights, psi, zs):
+    """(H psi)(z) for the given indices only (complex128 array)."""
+    lib = _load()
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    if psi.shape != (1 << H.n,):
+        raise ValueError("psi must have 2**n entries")
+    zs = np.ascontiguousarray(zs, dtype=np.uint64)
+    out = np.zeros(len(zs), dtype=np.complex128)
+    h, keep = H._ctypes()
+    w = (C.c_double * 3)(*[float(x) for x in weights])
+    rc = lib.or_hpsi_at(C.byref(h), w, psi.ctypes.data, len(zs), zs.ctypes.data, out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("or_hpsi_at failed")
     return out
 
 

@@ -1,0 +1,89 @@
+"""Planted mistakes in the oracle (on the CPU): each plausible error — a wrong sign, a dropped
+term, a wrong coefficient, a wrong stage time, a transposed index — is written into a temporary
+copy of the C oracle, and at least one pin of tests/test_oracle_pins.py must fail with it.
+This shows the pins are sharp enough to catch mistakes anywhere in the oracle."""
+import ctypes as C
+import os
+import subprocess
+
+import pytest
+
+import test_oracle_pins as pins
+from oracle import oracle as O
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "aqc_oracle.c")
+
+MUTATIONS = {
+    "sigma_y_sign": ("*re = -i * sign;", "*re = i * sign;"),
+    "indicator_penalty": ("return k == 1 ? 0.0 : 1.0;", "return k == 1 ? 1.0 : 0.0;"),
+    "scatter_at_source": ("jb->out[2 * zout] += c * re;", "jb->out[2 * z] += c * re;"),
+    "minus_i_sign": ("f[2 * z] = tmp[2 * z + 1];", "f[2 * z] = -tmp[2 * z + 1];"),
+    "rk4_stage_time": ("if (deriv(H, sc, t + 0.5 * h, ys, k, tmp, N, nthreads)) goto fail;",
+                       "if (deriv(H, sc, t + h, ys, k, tmp, N, nthreads)) goto fail;"),
+    "rk4_weight": ("psi[i] += (h / 6.0) * acc[i];", "psi[i] += (h / 5.0) * acc[i];"),
+    "predictor_dropped_term": ("+ 37.0 * fn2[i] - 9.0 * fn3[i]);", "+ 37.0 * fn2[i]);"),
+    "corrector_coefficient": ("+ 19.0 * fn[i] - 5.0 * fn1[i]", "+ 18.0 * fn[i] - 5.0 * fn1[i]"),
+    "smoothstep": ("s = 3.0 * tau * tau - 2.0 * tau * tau * tau;", "s = 3.0 * tau * tau - 2.0 * tau * tau;"),
+}
+
+PINS = [
+    lambda: pins.test_hpsi_matches_dense(4),
+    lambda: pins.test_final_hamiltonian_ground_state_brute_force(8, 1),
+    pins.test_golden_bit_order_and_clauses,
+    pins.test_rk4_startup_is_fourth_order_taylor,
+    lambda: pins.test_constant_hamiltonian_matches_exponential(3),
+    pins.test_landau_zener,
+    lambda: pins.test_product_state_time_dependent(0),
+    lambda: pins.test_product_state_time_dependent(1),
+    pins.test_x_driver_ground_state_and_spectrum,
+    pins.test_c_schedule_weights_closed_form,
+]
+
+
+def _mutant(tmp_path, name):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, name
+    mut = src.replace(old, new, 1)
+    c_path = tmp_path / f"{name}.c"
+    so_path = tmp_path / f"{name}.so"
+    c_path.write_text(mut)
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so_path), str(c_path),
+                           "-lpthread", "-lm"])
+    return str(so_path)
+
+
+def _bind(path):
+    lib = C.CDLL(path)
+    lib.or_hpsi.argtypes = [C.POINTER(O._Ham), C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_int]
+    lib.or_hpsi.restype = C.c_int
+    lib.or_propagate.argtypes = [C.POINTER(O._Ham), C.POINTER(O._Sched), C.c_int64, C.c_int64, C.c_void_p,
+                                 C.POINTER(O._Stats), C.c_int]
+    lib.or_propagate.restype = C.c_int
+    lib.or_hpsi_at.argtypes = [C.POINTER(O._Ham), C.POINTER(C.c_double), C.c_void_p, C.c_int64, C.c_void_p,
+                               C.c_void_p]
+    lib.or_hpsi_at.restype = C.c_int
+    lib.or_weights.argtypes = [C.POINTER(O._Sched), C.c_double, C.POINTER(C.c_double)]
+    lib.or_weights.restype = None
+    return lib
+
+
+def test_unmutated_oracle_passes_the_battery():
+    O._load()
+    for p in PINS:
+        p()
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(tmp_path, monkeypatch, name):
+    lib = _bind(_mutant(tmp_path, name))
+    monkeypatch.setattr(O, "_lib", lib)
+    failed = []
+    for i, p in enumerate(PINS):
+        try:
+            p()
+        except AssertionError:
+            failed.append(i)
+        except RuntimeError:
+            failed.append(i)
+    assert failed, f"no pin caught the planted mistake {name}"

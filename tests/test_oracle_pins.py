@@ -88,6 +88,18 @@ def test_hpsi_matches_dense(n):
         assert np.max(np.abs(got - ref)) < 1e-13
 
 
+@pytest.mark.parametrize("n", [3, 6, 9])
+def test_hpsi_at_matches_dense_and_full(n):
+    """Single-output evaluation equals the dense matrix row and the full scatter matvec."""
+    H = _random_pauli_ham(n, 300 + n, nterms=20)
+    w = [0.7, -0.2, 1.3]
+    psi = random_state(n, 9)
+    zs = np.arange(1 << n)
+    got = O.hpsi_at(H, w, psi, zs)
+    assert np.max(np.abs(got - O.dense_matrix(H, w) @ psi)) < 1e-13
+    assert np.max(np.abs(got - O.hpsi(H, w, psi))) < 1e-13
+
+
 def test_hpsi_threads_identical():
     H = _random_pauli_ham(9, 7, nterms=30, nclauses=8)
     psi = random_state(9, 3)
@@ -259,16 +271,18 @@ def test_landau_zener():
     assert abs(p_dia - ref) < 6e-3, (p_dia, ref)
 
 
-def _single_qubit_reference(a0, a1, bz0, bz1, T, psi0, M=20000):
-    """2x2 evolution under H(t) = (a0 + a1 t/T) X + (bz0 + bz1 t/T) Z by a product of exact
-    2x2 exponentials at midpoints (second order), refined by Richardson extrapolation."""
+def _single_qubit_reference(a0, a1, bz0, bz1, T, psi0, M=20000, smooth=False):
+    """2x2 evolution under H(t) = (a0 + a1 s) X + (bz0 + bz1 s) Z, s = t/T or 3 tau^2 - 2 tau^3,
+    by a product of exact 2x2 exponentials at midpoints (second order), refined by Richardson
+    extrapolation."""
     def run(M):
         psi = np.array(psi0, complex)
         h = T / M
         for k in range(M):
             t = (k + 0.5) * h
-            ax = a0 + a1 * t / T
-            bz = bz0 + bz1 * t / T
+            sv = t / T if not smooth else (t / T) ** 2 * (3 - 2 * t / T)
+            ax = a0 + a1 * sv
+            bz = bz0 + bz1 * sv
             r = math.hypot(ax, bz)
             # exp(-i h (ax X + bz Z)) = cos(hr) I - i sin(hr)/r (ax X + bz Z)
             c, s = math.cos(h * r), (math.sin(h * r) / r if r > 0 else h)
@@ -280,9 +294,11 @@ def _single_qubit_reference(a0, a1, bz0, bz1, T, psi0, M=20000):
     return (4 * b - a) / 3
 
 
-def test_product_state_time_dependent():
+@pytest.mark.parametrize("s_kind", [0, 1])
+def test_product_state_time_dependent(s_kind):
     """Non-interacting H(s) = (1-s) sum c_i (1 - X_i) + s sum b_i Z_i factorises; the oracle's
-    n-qubit solution equals the Kronecker product of single-qubit solutions."""
+    n-qubit solution equals the Kronecker product of single-qubit solutions (s = t/T and the
+    smoothstep s(t))."""
     n = 5
     rng = np.random.default_rng(5)
     c = rng.uniform(0.3, 1.0, n)
@@ -292,7 +308,7 @@ def test_product_state_time_dependent():
     O.add_x_driver(H, 0, list(c))
     for i in range(n):
         H.add_term(1, 0, 1 << i, b[i])
-    sched = O.linear_path(T)
+    sched = O.linear_path(T, s_kind)
     psi0 = O.uniform_state(n)
     N = O.step_count(H, sched, kappa=0.02)
     got = O.propagate(H, sched, N, psi0).psi
@@ -301,8 +317,9 @@ def test_product_state_time_dependent():
     phase = 0.0
     for q in range(n):
         # (1-s) c (I - X) + s b Z = (1-s) c I + [-(1-s) c] X + [s b] Z
-        phase += c[q] * T / 2  # integral of (1 - t/T) c over [0, T]
-        psi_q = _single_qubit_reference(-c[q], c[q], 0.0, b[q], T, np.array([1, 1]) / math.sqrt(2))
+        phase += c[q] * T / 2  # integral of (1 - s(t)) c over [0, T] (both s(t) average 1/2)
+        psi_q = _single_qubit_reference(-c[q], c[q], 0.0, b[q], T, np.array([1, 1]) / math.sqrt(2),
+                                        smooth=(s_kind == 1))
         full = np.kron(psi_q, full)  # qubit q is bit q: later qubits are more significant
     ref = full * np.exp(-1j * phase)
     assert np.linalg.norm(got - ref) < 1e-8
@@ -350,6 +367,21 @@ def test_step_count_rule():
     J = sum(abs(p[2]) for p in pairs)
     lam = max(abs(1 - s) * 10 + s * inst.m + s * (1 - s) * J for s in np.linspace(0, 1, 1025))
     assert O.step_count(Hc, O.nonlinear_path(10.0)) == math.ceil(10.0 * lam / O.KAPPA)
+
+
+def test_c_schedule_weights_closed_form():
+    """The C oracle's w_g(s(t)) for both s(t) against the closed forms."""
+    import ctypes as C
+
+    lib = O._load()
+    for kind in (0, 1):
+        sc = O.nonlinear_path(8.0, kind, alpha=2.0)._ctypes()
+        for t in (0.0, 1.0, 2.5, 4.0, 6.5, 8.0):
+            w = (C.c_double * 3)()
+            lib.or_weights(C.byref(sc), t, w)
+            tau = t / 8.0
+            s = tau if kind == 0 else 3 * tau * tau - 2 * tau ** 3
+            assert abs(w[0] - (1 - s)) < 1e-15 and abs(w[1] - s) < 1e-15 and abs(w[2] - 2 * s * (1 - s)) < 1e-15
 
 
 def test_smoothstep_schedule_weights():
