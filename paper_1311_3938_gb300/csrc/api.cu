@@ -43,14 +43,24 @@ std::vector<Layout> layouts_for(int n, int prec, int tile_bits) {
     ls.push_back(Layout{n, n, 0, n});
     return ls;
   }
-  // every layout gets full-size tiles: the last one overlaps its predecessor if needed
+  // every layout gets full-size tiles; when fewer high bits than a full strided layout holds
+  // are left, the last layout takes a longer contiguous run instead (fewer rows per tile, so
+  // fewer memory pages per tile), or overlaps its predecessor if that run would not fit
   ls.push_back(Layout{tmax, tmax, 0, tmax});
   const int w = tmax - cc;
   int start = tmax;
   while (start < n) {
-    const int h = std::min(start, n - w);
-    ls.push_back(Layout{cc, h, w, cc + w});
-    start = h + w;
+    const int left = n - start;
+    if (left >= w) {
+      ls.push_back(Layout{cc, start, w, cc + w});
+      start += w;
+    } else if (tmax - left <= start) {
+      ls.push_back(Layout{tmax - left, start, left, tmax});
+      start = n;
+    } else {
+      ls.push_back(Layout{cc, n - w, w, cc + w});
+      start = n;
+    }
   }
   return ls;
 }
@@ -215,16 +225,22 @@ int build_tables(aqc_ctx* c) {
   for (int l = 0; l <= nl; l++) {
     t->flip_begin[l] = pos;
     if (pos + (int)per[l].size() > kMaxFlips) FAIL(c, AQC_E_UNSUPPORTED, "more than %d off-diagonal products", kMaxFlips);
-    // X strings with real coefficients first (the kernel's fast loop), then general products
-    int np = 0;
+    // X strings with real coefficients first (the kernel's fast loops: those flipping no
+    // register-held tile bit, then the others), then general products
+    int np = 0, nfast = 0;
     if (l < nl) {
+      const uint32_t regbits = c->prec == AQC_C128 ? kRegBitsC128 : kRegBitsC64;
       for (const DevFlip& f : per[l])
-        if (f.zm == 0) t->flips[pos + np++] = f;
+        if (f.zm == 0 && (f.lx & regbits) == 0) t->flips[pos + np++] = f;
+      nfast = np;
+      for (const DevFlip& f : per[l])
+        if (f.zm == 0 && (f.lx & regbits) != 0) t->flips[pos + np++] = f;
     }
     int k = np;
     for (const DevFlip& f : per[l])
       if (l == nl || f.zm != 0) t->flips[pos + k++] = f;
     t->plain_count[l] = np;
+    t->plain_fast[l] = nfast;
     if (l < nl) {
       c->nplain[l] = np;
       c->ngeneral[l] = (int)per[l].size() - np;
@@ -328,18 +344,18 @@ ApplyParams base_params(aqc_ctx* c) {
 }
 
 // One evaluation of H(t) src over all layouts.  The strided layouts run first as partial sums
-// (the first one also adds the diagonal and the products no layout holds); the contiguous
-// layout 0 runs last with the mode epilogue, so the kernel touching the most vectors has the
-// smallest page footprint per tile.
+// (the first one also adds the products no layout holds); the contiguous layout 0 runs last
+// with the mode epilogue, so the kernel touching the most vectors has the smallest page
+// footprint per tile.  The diagonal is added by layout 0 (see diag_level).
 int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, void* partial_out) {
   const int nl = (int)c->layouts.size();
   for (int step = 0; step < nl; step++) {
     const int l = nl - 1 - step;
-    const bool first = (step == 0), last = (l == 0);
+    const bool first = (step == 0), last = (l == 0), diag = (l == diag_level(nl));
     ApplyParams p = last ? fin : base_params(c);
     p.L = c->layouts[l];
     p.layout_index = l;
-    p.with_diag = first;
+    p.with_diag = diag;
     p.with_remote = first;
     for (int g = 0; g < 3; g++) p.w[g] = w[g];
     p.src = src;
@@ -350,10 +366,10 @@ int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, vo
     } else if (fin.mode == MODE_PARTIAL) {
       p.qout = partial_out;
     }
-    p.dcode = (first && c->table_class >= 0) ? c->d_dcode : nullptr;
+    p.dcode = (diag && c->table_class >= 0) ? c->d_dcode : nullptr;
     p.ntiles = 1u << (c->n - p.L.t);
     const size_t smem = apply_smem_bytes(c->prec, p.L.t, c->nplain[l], c->ngeneral[l] + (first ? c->n_remote : 0),
-                                         first ? c->n_z : 0);
+                                         diag ? c->n_z : 0);
     if (smem > 227 * 1024) FAIL(c, AQC_E_UNSUPPORTED, "shared memory %zu bytes too large", smem);
     CUDA_TRY(c, launch_apply(c->prec, p, (int)smem, c->stream));
     c->launches++;
@@ -542,9 +558,9 @@ int batch_rebuild(aqc_batch* b) {
       if (l == 0) I.item_begin = (uint32_t)items[0].size();
       for (uint32_t t = 0; t < ntiles; t++) items[l].push_back(BatchItem{(uint32_t)slot, t});
       if (l == 0) I.item_end = (uint32_t)items[0].size();
-      const bool first = (l == nl - 1);
+      const bool first = (l == nl - 1), diag = (l == diag_level(nl));
       const size_t sm = apply_smem_bytes(c->prec, c->layouts[l].t, c->nplain[l],
-                                         c->ngeneral[l] + (first ? c->n_remote : 0), first ? c->n_z : 0);
+                                         c->ngeneral[l] + (first ? c->n_remote : 0), diag ? c->n_z : 0);
       if (sm > 227 * 1024) BFAIL(b, AQC_E_UNSUPPORTED, "shared memory %zu bytes too large", sm);
       smem[l] = std::max(smem[l], (int)sm);
     }

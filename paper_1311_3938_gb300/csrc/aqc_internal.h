@@ -47,6 +47,7 @@ struct DevTables {
   int n_remote;                     // flips no layout holds, gathered from global memory
   int flip_begin[kMaxLayouts + 2];  // layout l: [flip_begin[l], flip_begin[l+1]); remote after
   int plain_count[kMaxLayouts + 2]; // leading X-string products (zm = 0, real) of each range
+  int plain_fast[kMaxLayouts + 2];  // of those, the leading ones that flip no register-held tile bit
   int n_z;
   int n_classes;
   int table_class;                  // clause class whose counts are in the per-index byte table, or -1
@@ -126,6 +127,20 @@ struct BatchLaunch {
   double* partials;  // two doubles per level-0 item
   int level;
 };
+
+// Which layout pass of an evaluation adds the diagonal: layout 0, the last pass (the fused step
+// kernel in a propagation, memory-bound with issue slots to spare; its clause bytes are staged
+// in shared memory with the tile).  The first pass (the highest layout) adds the products no
+// layout holds.
+__host__ __device__ inline int diag_level(int n_layouts) {
+  (void)n_layouts;
+  return 0;
+}
+
+// Tile bits a thread holds in registers (see process_tile): bit 0 and bit 6 for complex64 (two
+// halves of two amplitudes, 64 indices apart), bit 5 for complex128 (two single amplitudes).
+constexpr uint32_t kRegBitsC64 = 0x41u;
+constexpr uint32_t kRegBitsC128 = 0x20u;
 
 // result slots (doubles) in the workspace
 constexpr int kSlotNorm2 = 0;

@@ -62,13 +62,14 @@ struct SZ {
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-// dynamic shared memory map of k_apply: [tile][plain flips][general flips][Z strings][reduction]
+// dynamic shared memory map of k_apply: [tile][clause bytes][plain flips][general flips][Z strings][reduction]
 template <typename R>
 struct SmemMap {
-  size_t pf, gf, zs, red, total;
+  size_t code, pf, gf, zs, red, total;
   __host__ __device__ SmemMap(uint32_t tsize, int np, int ng, int nz) {
     using C2 = typename Cplx<R>::T;
-    pf = align16((size_t)tsize * sizeof(C2));
+    code = align16((size_t)tsize * sizeof(C2));  // the tile's clause bytes
+    pf = align16(code + (size_t)tsize);
     gf = align16(pf + (size_t)np * sizeof(PFlip<R>));
     zs = align16(gf + (size_t)ng * sizeof(SFlip<R>));
     red = align16(zs + (size_t)nz * sizeof(SZ<R>));
@@ -161,8 +162,6 @@ __device__ __forceinline__ R clause_count(const DevTables* __restrict__ tab, con
 }
 
 constexpr int kThreads = 256;
-constexpr int kVf = 4;  // points per thread held in registers while the term loop runs (FP32)
-constexpr int kVd = 2;  // the same for FP64 (the FP64 pipe, not memory, bounds that path)
 
 // 16-byte global -> shared copies that do not pass through registers (many in flight per thread)
 __device__ __forceinline__ void cp_async16(void* smem_ptr, const void* gptr) {
@@ -180,7 +179,7 @@ struct TileCtx {
   using C2 = typename Cplx<R>::T;
   Layout L;
   uint32_t tsize, tmask;
-  int np, ngl, ng, nz, ncls, tcls, stage;
+  int np, npf, ngl, ng, nz, ncls, tcls, stage;
   R dconst, wtab, h;
   const DevTables* tab;
   const uint8_t* dcode;
@@ -188,6 +187,7 @@ struct TileCtx {
   const C2 *src, *qin, *f0, *f1, *f2;
   C2 *qout, *y, *fout, *pout, *acc;
   C2* s_p;
+  uint8_t* s_code;
   PFlip<R>* s_pf;
   SFlip<R>* s_gf;
   SZ<R>* s_z;
@@ -210,6 +210,7 @@ __device__ __forceinline__ void load_coefficients(TileCtx<R>& T, const DevTables
   T.w2 = w2;
   const int fb = tab->flip_begin[li];
   T.np = tab->plain_count[li];
+  T.npf = tab->plain_fast[li];
   T.ngl = tab->flip_begin[li + 1] - fb - T.np;
   const int rb = tab->flip_begin[tab->n_layouts];
   const int nrem = with_remote ? tab->n_remote : 0;
@@ -217,6 +218,7 @@ __device__ __forceinline__ void load_coefficients(TileCtx<R>& T, const DevTables
   T.nz = with_diag ? tab->n_z : 0;
   const SmemMap<R> map(T.tsize, T.np, T.ng, T.nz);
   T.s_p = reinterpret_cast<typename TileCtx<R>::C2*>(smem);
+  T.s_code = smem + map.code;
   T.s_pf = reinterpret_cast<PFlip<R>*>(smem + map.pf);
   T.s_gf = reinterpret_cast<SFlip<R>*>(smem + map.gf);
   T.s_z = reinterpret_cast<SZ<R>*>(smem + map.zs);
@@ -270,15 +272,52 @@ __device__ __forceinline__ void load_coefficients(TileCtx<R>& T, const DevTables
   }
 }
 
+// Points of one thread: two "halves" of H consecutive tile indices (16 bytes each: H = 2
+// complex64 or 1 complex128), the second half HB = 32 H indices after the first.  Lanes of a warp
+// take consecutive halves, so every global and shared access of a warp is 512 contiguous bytes
+// (coalesced, bank-conflict free) and moves as 16-byte vectors.  Products flipping only the bits
+// inside a half (tile bit 0 for complex64) or the half bit (tile bit log2 HB) are register
+// permutations; every other product is one 16-byte shared-memory load per half.
+template <typename R>
+struct Blk;
+template <>
+struct Blk<float> {
+  static constexpr int H = 2;
+};
+template <>
+struct Blk<double> {
+  static constexpr int H = 1;
+};
+
+template <typename C2, int H>
+__device__ __forceinline__ void ld16(const C2* __restrict__ a, uint32_t i, C2 (&v)[H]) {
+  const float4 x = *reinterpret_cast<const float4*>(a + i);
+  const C2* xs = reinterpret_cast<const C2*>(&x);
+#pragma unroll
+  for (int q = 0; q < H; q++) v[q] = xs[q];
+}
+
+template <typename C2, int H>
+__device__ __forceinline__ void st16(C2* __restrict__ a, uint32_t i, const C2* v) {
+  float4 x;
+  C2* xs = reinterpret_cast<C2*>(&x);
+#pragma unroll
+  for (int q = 0; q < H; q++) xs[q] = v[q];
+  *reinterpret_cast<float4*>(a + i) = x;
+}
+
 // One tile: stage the source tile in shared memory, then for every point of the tile compute
 // acc = q + diagonal + products, and run the mode epilogue.  rt0/rt1 collect the reduction
 // partials of this thread in the state precision.
 template <typename R, int MODE>
 __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile, R& rt0, R& rt1) {
   using C2 = typename Cplx<R>::T;
+  constexpr int H = Blk<R>::H;
+  constexpr int G = 2 * H;
+  constexpr uint32_t HM = H - 1;
+  constexpr uint32_t HB = 32 * H;
   constexpr bool kNeedY = (MODE == MODE_STEP || MODE == MODE_RK4);
   constexpr bool kNeedF = (MODE == MODE_STEP);
-  constexpr int kV = sizeof(R) == 4 ? kVf : kVd;
   const C2 zero2 = C2{(R)0, (R)0};
   const Layout L = T.L;
   const uint32_t tsize = T.tsize, tmask = T.tmask;
@@ -289,6 +328,7 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
   // complex64 (tile bit 0 is global bit 0), one index for complex128
   __syncthreads();  // readers of the previous tile (or of the coefficients' writers) are done
   const uint32_t zb = tile_base(L, tile);
+  const bool code_smem = T.tcls >= 0 && L.c >= 4 && tsize >= 16;
   {
     constexpr uint32_t per16 = 16 / sizeof(C2);  // indices per 16-byte granule
     const uint32_t granules = tsize / per16;
@@ -296,146 +336,336 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
       const uint32_t j = g * per16;
       cp_async16(s_p + j, src + tile_z(L, j, zb));
     }
+    if (code_smem) {  // the clause bytes of the tile, 16 contiguous indices per copy
+      for (uint32_t g = threadIdx.x; g < (tsize >> 4); g += blockDim.x) {
+        const uint32_t j = g << 4;
+        cp_async16(T.s_code + j, T.dcode + tile_z(L, j, zb));
+      }
+    }
     cp_async_wait_all();
   }
   __syncthreads();
 
-  for (uint32_t base = threadIdx.x; base < tsize; base += blockDim.x * kV) {
-    uint32_t jm[kV], z[kV];
-    bool ok[kV];
+  const bool full = tsize >= 2 * HB;  // every state with more than 6 (complex64) / 5 qubits
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // the partial sum q and the clause bytes of a block are fetched one iteration ahead (software
+  // pipelining), so their latency overlaps the previous block's work
+  C2 pq[G];
+  uint32_t pc[G];
+  auto fetch_qc = [&](uint32_t itn) {
+    if (!full || itn * 2 * HB >= tsize) return;
 #pragma unroll
-    for (int v = 0; v < kV; v++) {
-      const uint32_t j = base + (uint32_t)v * blockDim.x;
-      ok[v] = j < tsize;
-      jm[v] = j & tmask;
-      z[v] = tile_z(L, jm[v], zb);
-    }
-    // 1. issue this chunk's pointwise global loads first; they complete while the
-    //    shared-memory gathers below run
-    C2 qv[kV], y0[kV], a[kV], b[kV], c[kV];
-    uint32_t code[kV];
+    for (int k = 0; k < 2; k++) {
+      const uint32_t zk = tile_z(L, (itn * 2 * HB + k * HB + lane * H) & tmask, zb);
+      if (T.qin) {
+        C2 t[H];
+        ld16<C2, H>(T.qin, zk, t);
 #pragma unroll
-    for (int v = 0; v < kV; v++) {
-      qv[v] = (T.qin && ok[v]) ? T.qin[z[v]] : zero2;
-      code[v] = (T.tcls >= 0 && ok[v]) ? (uint32_t)T.dcode[z[v]] : 0u;
-      if (kNeedY) y0[v] = ok[v] ? T.y[z[v]] : zero2;
-      if (kNeedF) {
-        a[v] = ok[v] ? T.f0[z[v]] : zero2;
-        b[v] = ok[v] ? T.f1[z[v]] : zero2;
-        c[v] = ok[v] ? T.f2[z[v]] : zero2;
-      } else if (MODE == MODE_RK4) {
-        a[v] = (ok[v] && T.stage > 1) ? T.acc[z[v]] : zero2;
+        for (int q = 0; q < H; q++) pq[k * H + q] = t[q];
+      }
+      if (T.tcls >= 0 && !code_smem) {
+        if (H == 2) {
+          const uint32_t w2 = *reinterpret_cast<const uint16_t*>(T.dcode + zk);
+          pc[k * H] = w2 & 0xffu;
+          pc[k * H + (H - 1)] = (w2 >> 8) & 0xffu;
+        } else {
+          pc[k * H] = T.dcode[zk];
+        }
       }
     }
-    // 2. X strings with real coefficients: shared-memory gathers
-    R ar[kV], ai[kV];
+  };
+  fetch_qc(warp);
+  for (uint32_t it = warp; it * 2 * HB < tsize; it += nwarps) {
+    uint32_t jh[2], zh[2];
+    jh[0] = (it * 2 * HB + lane * H) & tmask;
+    jh[1] = (it * 2 * HB + HB + lane * H) & tmask;
+    bool ok[G];
+    uint32_t z[G];
 #pragma unroll
-    for (int v = 0; v < kV; v++) {
-      ar[v] = (R)0;
-      ai[v] = (R)0;
+    for (int k = 0; k < 2; k++) {
+      zh[k] = tile_z(L, jh[k], zb);
+#pragma unroll
+      for (int q = 0; q < H; q++) {
+        const uint32_t jj = it * 2 * HB + k * HB + lane * H + q;
+        ok[k * H + q] = jj < tsize;
+        z[k * H + q] = full ? zh[k] + q : tile_z(L, jj & tmask, zb);
+      }
     }
-    for (int k = 0; k < T.np; k++) {
-      const PFlip<R> f = T.s_pf[k];
+    // 1. pointwise global loads first; they complete while the shared-memory gathers run
+    C2 qv[G], y0[G], a[G], b[G], c[G];
+    uint32_t code[G];
+    if (full) {
 #pragma unroll
-      for (int v = 0; v < kV; v++) {
-        const C2 u = s_p[jm[v] ^ f.lx];
-        ar[v] += f.c * u.x;
-        ai[v] += f.c * u.y;
+      for (int g = 0; g < G; g++) {
+        qv[g] = pq[g];
+        code[g] = pc[g];
+      }
+      if (code_smem) {
+#pragma unroll
+        for (int k = 0; k < 2; k++)
+#pragma unroll
+          for (int q = 0; q < H; q++) code[k * H + q] = T.s_code[jh[k] + q];
+      }
+      fetch_qc(it + nwarps);
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        C2 t[H];
+        if (kNeedY) {
+          ld16<C2, H>(T.y, zh[k], t);
+#pragma unroll
+          for (int q = 0; q < H; q++) y0[k * H + q] = t[q];
+        }
+        if (kNeedF) {
+          ld16<C2, H>(T.f0, zh[k], t);
+#pragma unroll
+          for (int q = 0; q < H; q++) a[k * H + q] = t[q];
+          ld16<C2, H>(T.f1, zh[k], t);
+#pragma unroll
+          for (int q = 0; q < H; q++) b[k * H + q] = t[q];
+          ld16<C2, H>(T.f2, zh[k], t);
+#pragma unroll
+          for (int q = 0; q < H; q++) c[k * H + q] = t[q];
+        } else if (MODE == MODE_RK4) {
+          if (T.stage > 1) {
+            ld16<C2, H>(T.acc, zh[k], t);
+#pragma unroll
+            for (int q = 0; q < H; q++) a[k * H + q] = t[q];
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        qv[g] = (T.qin && ok[g]) ? T.qin[z[g]] : zero2;
+        if (kNeedY) y0[g] = ok[g] ? T.y[z[g]] : zero2;
+        if (kNeedF) {
+          a[g] = ok[g] ? T.f0[z[g]] : zero2;
+          b[g] = ok[g] ? T.f1[z[g]] : zero2;
+          c[g] = ok[g] ? T.f2[z[g]] : zero2;
+        } else if (MODE == MODE_RK4) {
+          a[g] = (ok[g] && T.stage > 1) ? T.acc[z[g]] : zero2;
+        }
+        code[g] = (T.tcls >= 0 && ok[g]) ? (uint32_t)T.dcode[z[g]] : 0u;
+      }
+    }
+    if (!T.qin) {
+#pragma unroll
+      for (int g = 0; g < G; g++) qv[g] = zero2;
+    }
+    // own values of the source
+    C2 own[G];
+    if (full) {
+      C2 t0[H], t1[H];
+      ld16<C2, H>(s_p, jh[0], t0);
+      ld16<C2, H>(s_p, jh[1], t1);
+#pragma unroll
+      for (int q = 0; q < H; q++) {
+        own[q] = t0[q];
+        own[H + q] = t1[q];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 2; k++)
+#pragma unroll
+        for (int q = 0; q < H; q++) own[k * H + q] = s_p[(jh[k] + q) & tmask];
+    }
+
+    // partner values u[g] = s(tile index of point g XOR lx); selects instead of runtime
+    // indexing keep everything in registers
+    auto gather = [&](uint32_t lx, C2 (&u)[G]) {
+      const uint32_t hi = lx & ~(HM | HB);
+      const bool mh = (lx & HM) != 0, sw = (lx & HB) != 0;
+      C2 part[G];
+      if (hi == 0) {
+#pragma unroll
+        for (int q = 0; q < H; q++) {
+          part[q] = sw ? own[H + q] : own[q];
+          part[H + q] = sw ? own[q] : own[H + q];
+        }
+      } else {
+        const uint32_t j0 = (sw ? jh[1] : jh[0]) ^ hi, j1 = (sw ? jh[0] : jh[1]) ^ hi;
+        if (full) {
+          C2 t0[H], t1[H];
+          ld16<C2, H>(s_p, j0, t0);
+          ld16<C2, H>(s_p, j1, t1);
+#pragma unroll
+          for (int q = 0; q < H; q++) {
+            part[q] = t0[q];
+            part[H + q] = t1[q];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < H; q++) {
+            part[q] = s_p[(j0 + q) & tmask];
+            part[H + q] = s_p[(j1 + q) & tmask];
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        if (H == 2) {
+          u[k * H] = mh ? part[k * H + (H - 1)] : part[k * H];
+          u[k * H + (H - 1)] = mh ? part[k * H] : part[k * H + (H - 1)];
+        } else {
+          u[k * H] = part[k * H];
+        }
+      }
+    };
+
+    // 2. X strings with real coefficients
+    R ar[G], ai[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      ar[g] = (R)0;
+      ai[g] = (R)0;
+    }
+    // products flipping no register-held bit: one 16-byte shared load per half, no selects
+    if (full) {
+      for (int kk = 0; kk < T.npf; kk++) {
+        const PFlip<R> f = T.s_pf[kk];
+        C2 t0[H], t1[H];
+        ld16<C2, H>(s_p, jh[0] ^ f.lx, t0);
+        ld16<C2, H>(s_p, jh[1] ^ f.lx, t1);
+#pragma unroll
+        for (int q = 0; q < H; q++) {
+          ar[q] += f.c * t0[q].x;
+          ai[q] += f.c * t0[q].y;
+          ar[H + q] += f.c * t1[q].x;
+          ai[H + q] += f.c * t1[q].y;
+        }
+      }
+    }
+    for (int kk = full ? T.npf : 0; kk < T.np; kk++) {
+      const PFlip<R> f = T.s_pf[kk];
+      C2 u[G];
+      gather(f.lx, u);
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        ar[g] += f.c * u[g].x;
+        ai[g] += f.c * u[g].y;
       }
     }
     // 3. general products (Y/Z phases, complex coefficients) and remote products
-    for (int k = 0; k < T.ng; k++) {
-      const SFlip<R> f = T.s_gf[k];
+    for (int kk = 0; kk < T.ng; kk++) {
+      const SFlip<R> f = T.s_gf[kk];
+      C2 u[G];
+      if (kk < T.ngl) {
+        gather(f.lx, u);
+      } else {
 #pragma unroll
-      for (int v = 0; v < kV; v++) {
-        C2 u;
-        if (k < T.ngl)
-          u = s_p[jm[v] ^ f.lx];
-        else
-          u = ok[v] ? src[z[v] ^ f.x] : zero2;
+        for (int g = 0; g < G; g++) u[g] = ok[g] ? src[z[g] ^ f.x] : zero2;
+      }
+#pragma unroll
+      for (int g = 0; g < G; g++) {
         R cr = f.cr, ci = f.ci;
-        if (__popc(f.zm & (z[v] ^ f.x)) & 1) {
+        if (__popc(f.zm & (z[g] ^ f.x)) & 1) {
           cr = -cr;
           ci = -ci;
         }
-        ar[v] += cr * u.x - ci * u.y;
-        ai[v] += cr * u.y + ci * u.x;
+        ar[g] += cr * u[g].x - ci * u[g].y;
+        ai[g] += cr * u[g].y + ci * u[g].x;
       }
     }
     // 4. diagonal and partial sum of the earlier layouts
     const bool with_diag = (T.nz > 0 || T.ncls > 0 || T.dconst != (R)0);
 #pragma unroll
-    for (int v = 0; v < kV; v++) {
+    for (int g = 0; g < G; g++) {
       if (with_diag) {
         R d = T.dconst;
-        if (T.tcls >= 0) d += T.wtab * (R)code[v];
+        if (T.tcls >= 0) d += T.wtab * (R)code[g];
         for (int cc = 0; cc < T.ncls; cc++) {
           if (cc == T.tcls) continue;
           const DevClass cl = T.tab->classes[cc];
-          d += (R)(cl.scale * pick3(T.w0, T.w1, T.w2, cl.group)) * clause_count<R>(T.tab, cl, z[v]);
+          d += (R)(cl.scale * pick3(T.w0, T.w1, T.w2, cl.group)) * clause_count<R>(T.tab, cl, z[g]);
         }
         for (int k = 0; k < T.nz; k++) {
           const SZ<R> e = T.s_z[k];
-          d += (__popc(e.zm & z[v]) & 1) ? -e.c : e.c;
+          d += (__popc(e.zm & z[g]) & 1) ? -e.c : e.c;
         }
-        const C2 pv = s_p[jm[v]];
-        ar[v] += d * pv.x;
-        ai[v] += d * pv.y;
+        ar[g] += d * own[g].x;
+        ai[g] += d * own[g].y;
       }
-      ar[v] += qv[v].x;
-      ai[v] += qv[v].y;
+      ar[g] += qv[g].x;
+      ai[g] += qv[g].y;
     }
     // 5. epilogue
     const R h = T.h;
     const R h24 = h / (R)24;
+    C2 o1[G], o2[G], o3[G];
 #pragma unroll
-    for (int v = 0; v < kV; v++) {
-      if (!ok[v]) continue;
-      const uint32_t zz = z[v];
+    for (int g = 0; g < G; g++) {
       if (MODE == MODE_PARTIAL) {
-        T.qout[zz] = C2{ar[v], ai[v]};
+        o1[g] = C2{ar[g], ai[g]};
       } else if (MODE == MODE_DERIV) {
-        T.fout[zz] = C2{ai[v], -ar[v]};  // -i (ar + i ai)
+        o1[g] = C2{ai[g], -ar[g]};  // -i (ar + i ai)
       } else if (MODE == MODE_ENERGY) {
-        const C2 pv = s_p[jm[v]];
-        rt0 += pv.x * ar[v] + pv.y * ai[v];
-        rt1 += pv.x * ai[v] - pv.y * ar[v];
+        if (ok[g]) {
+          rt0 += own[g].x * ar[g] + own[g].y * ai[g];
+          rt1 += own[g].x * ai[g] - own[g].y * ar[g];
+        }
       } else if (MODE == MODE_STEP) {
         // f_{n+1} = -i H p_{n+1};  corrector y_{n+1};  predictor p_{n+2}  (Sec. I.B)
-        const C2 fn = C2{ai[v], -ar[v]};
+        const C2 fn = C2{ai[g], -ar[g]};
         C2 yn, pn;
-        yn.x = y0[v].x + h24 * ((R)9 * fn.x + (R)19 * a[v].x - (R)5 * b[v].x + c[v].x);
-        yn.y = y0[v].y + h24 * ((R)9 * fn.y + (R)19 * a[v].y - (R)5 * b[v].y + c[v].y);
-        pn.x = yn.x + h24 * ((R)55 * fn.x - (R)59 * a[v].x + (R)37 * b[v].x - (R)9 * c[v].x);
-        pn.y = yn.y + h24 * ((R)55 * fn.y - (R)59 * a[v].y + (R)37 * b[v].y - (R)9 * c[v].y);
-        T.y[zz] = yn;
-        T.fout[zz] = fn;
-        T.pout[zz] = pn;
-        const C2 pv = s_p[jm[v]];
-        const R dx = yn.x - pv.x, dy = yn.y - pv.y;
-        rt0 += yn.x * yn.x + yn.y * yn.y;
-        rt1 += dx * dx + dy * dy;
+        yn.x = y0[g].x + h24 * ((R)9 * fn.x + (R)19 * a[g].x - (R)5 * b[g].x + c[g].x);
+        yn.y = y0[g].y + h24 * ((R)9 * fn.y + (R)19 * a[g].y - (R)5 * b[g].y + c[g].y);
+        pn.x = yn.x + h24 * ((R)55 * fn.x - (R)59 * a[g].x + (R)37 * b[g].x - (R)9 * c[g].x);
+        pn.y = yn.y + h24 * ((R)55 * fn.y - (R)59 * a[g].y + (R)37 * b[g].y - (R)9 * c[g].y);
+        o1[g] = yn;
+        o2[g] = fn;
+        o3[g] = pn;
+        if (ok[g]) {
+          const R dx = yn.x - own[g].x, dy = yn.y - own[g].y;
+          rt0 += yn.x * yn.x + yn.y * yn.y;
+          rt1 += dx * dx + dy * dy;
+        }
       } else if (MODE == MODE_RK4) {
-        const C2 k = C2{ai[v], -ar[v]};
+        const C2 k = C2{ai[g], -ar[g]};
         if (T.stage == 1) {
-          T.fout[zz] = k;
-          T.acc[zz] = k;
+          o1[g] = k;  // history f_n
+          o2[g] = k;  // accumulator
           const R hh = (R)0.5 * h;
-          T.pout[zz] = C2{y0[v].x + hh * k.x, y0[v].y + hh * k.y};
+          o3[g] = C2{y0[g].x + hh * k.x, y0[g].y + hh * k.y};
         } else if (T.stage == 2 || T.stage == 3) {
-          C2 s2 = a[v];
+          C2 s2 = a[g];
           s2.x += (R)2 * k.x;
           s2.y += (R)2 * k.y;
-          T.acc[zz] = s2;
+          o2[g] = s2;
           const R hh = T.stage == 2 ? (R)0.5 * h : h;
-          T.pout[zz] = C2{y0[v].x + hh * k.x, y0[v].y + hh * k.y};
+          o3[g] = C2{y0[g].x + hh * k.x, y0[g].y + hh * k.y};
         } else {
-          C2 s2 = a[v];
+          C2 s2 = a[g];
           s2.x += k.x;
           s2.y += k.y;
           const R h6 = h / (R)6;
-          T.y[zz] = C2{y0[v].x + h6 * s2.x, y0[v].y + h6 * s2.y};
+          o1[g] = C2{y0[g].x + h6 * s2.x, y0[g].y + h6 * s2.y};
         }
+      }
+    }
+    // stores
+    if (MODE == MODE_ENERGY) continue;
+    C2* d1 = MODE == MODE_PARTIAL ? T.qout : (MODE == MODE_DERIV ? T.fout : (MODE == MODE_STEP ? T.y : nullptr));
+    C2* d2 = MODE == MODE_STEP ? T.fout : nullptr;
+    C2* d3 = MODE == MODE_STEP ? T.pout : nullptr;
+    if (MODE == MODE_RK4) {
+      d1 = T.stage == 1 ? T.fout : (T.stage == 4 ? T.y : nullptr);
+      d2 = T.stage <= 3 ? T.acc : nullptr;
+      d3 = T.stage <= 3 ? T.pout : nullptr;
+    }
+    if (full) {
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        if (d1) st16<C2, H>(d1, zh[k], o1 + k * H);
+        if (d2) st16<C2, H>(d2, zh[k], o2 + k * H);
+        if (d3) st16<C2, H>(d3, zh[k], o3 + k * H);
+      }
+    } else {
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        if (!ok[g]) continue;
+        if (d1) d1[z[g]] = o1[g];
+        if (d2) d2[z[g]] = o2[g];
+        if (d3) d3[z[g]] = o3[g];
       }
     }
   }
@@ -499,7 +729,7 @@ __device__ __forceinline__ double batch_weight(const BatchInst& I, double s, int
 // MODE_STEP), with per-member reductions summed by the member's last CTA, which then advances
 // the member's step counter.
 template <typename R, int NT>
-__global__ void __launch_bounds__(NT) k_batch(BatchLaunch B) {
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_batch(BatchLaunch B) {
   using C2 = typename Cplx<R>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   const BatchItem it = B.items[blockIdx.x];
@@ -512,8 +742,8 @@ __global__ void __launch_bounds__(NT) k_batch(BatchLaunch B) {
   const double s = I->s_kind == 1 ? tau * tau * (3.0 - 2.0 * tau) : tau;
   TileCtx<R> T;
   const bool first = (level == nl - 1);  // first layout pass of this member's evaluation
-  load_coefficients<R>(T, I->tab, I->layouts[level], level, first, first, I->dcode, batch_weight(*I, s, 0),
-                       batch_weight(*I, s, 1), batch_weight(*I, s, 2), smem);
+  load_coefficients<R>(T, I->tab, I->layouts[level], level, level == diag_level(nl), first, I->dcode,
+                       batch_weight(*I, s, 0), batch_weight(*I, s, 1), batch_weight(*I, s, 2), smem);
   T.stage = 0;
   T.h = (R)I->h;
   C2* const* v = reinterpret_cast<C2* const*>(I->vec);

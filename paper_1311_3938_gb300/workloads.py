@@ -202,10 +202,12 @@ class Server:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0  # noqa: E731
+        prof = {"admit_s": 0.0, "advance_s": 0.0, "poll_s": 0.0, "retire_s": 0.0, "rounds": 0}
         while pending or in_batch or big:
             if time_limit and now() > time_limit:
                 break
             # admission: FIFO among arrived jobs, as memory allows
+            ta = time.perf_counter()
             while pending and pending[0].arrival <= now():
                 job = pending[0]
                 need = job.workspace_bytes()
@@ -224,12 +226,15 @@ class Server:
                     stream = torch.cuda.Stream(self.device)
                     ctx, inst = make_context(job, self.device, stream=stream)
                     big.append([job, ctx, inst, stream, None, 0])
+            prof["admit_s"] += time.perf_counter() - ta
             self.occupancy.append(self.used / max(1, self.budget))
             if not in_batch and not big:
                 if pending:
                     time.sleep(min(0.01, max(0.0, pending[0].arrival - now())))
                 continue
             # advance: one batch round and one chunk per large job, on different streams
+            ta = time.perf_counter()
+            prof["rounds"] += 1
             if in_batch:
                 self.batch.run(1)
             for entry in big:
@@ -241,9 +246,14 @@ class Server:
                     if entry[5] >= _nsteps(ctx, job):
                         entry[4] = torch.cuda.Event()
                         entry[4].record(stream)
+            prof["advance_s"] += time.perf_counter() - ta
             # retire finished work
+            ta = time.perf_counter()
             if in_batch:
                 steps, _, _ = self.batch.poll()
+            prof["poll_s"] += time.perf_counter() - ta
+            ta = time.perf_counter()
+            if in_batch:
                 for slot in list(in_batch):
                     job, ctx, inst = in_batch[slot]
                     if steps[slot] >= _nsteps(ctx, job):
@@ -267,6 +277,7 @@ class Server:
                     self.used -= job.workspace_bytes()
                     big.remove(entry)
                     done.append(job)
+            prof["retire_s"] += time.perf_counter() - ta
         wall = now()
         lat = np.array([j.latency for j in done]) if done else np.array([math.nan])
         return {
@@ -278,6 +289,7 @@ class Server:
             "hbm_budget_bytes": self.budget,
             "hbm_peak_bytes": self.peak_used,
             "hbm_mean_occupancy": float(np.mean(self.occupancy)) if self.occupancy else 0.0,
+            "loop": prof,
             "jobs": done,
         }
 
