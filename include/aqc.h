@@ -135,7 +135,10 @@ int aqc_get_grid(aqc_ctx *ctx, int64_t *n_steps, double *h);
 
 /* Tile size of the shared-memory tiles (2^tile_bits amplitudes per CTA tile; 0 = default:
  * 13 for AQC_C64, 12 for AQC_C128; allowed 6..13 / 5..12).  Smaller tiles give more CTAs for
- * small states but more layout passes for large ones.  Resets the integrator. */
+ * small states but more layout passes for large ones.  For AQC_C64 states of 22..28 qubits,
+ * 16 selects cluster tiles: 2^16 amplitudes spread over a cluster of 8 CTAs that read each
+ * other's shared memory, so two layout passes cover every bit (per-CTA tiles need three).
+ * Batch members always use per-CTA tiles.  Resets the integrator. */
 int aqc_set_tile_bits(aqc_ctx *ctx, int tile_bits);
 
 /* Set psi(0) and reset the integrator to t = 0.  kind = AQC_INIT_*; `basis` for

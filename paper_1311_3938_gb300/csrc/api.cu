@@ -36,9 +36,26 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int tile_bits_max(int prec) { return prec == AQC_C128 ? 12 : 13; }
 int chunk_bits(int prec) { return prec == AQC_C128 ? 4 : 5; }  // 256-byte contiguous chunks
 
-std::vector<Layout> layouts_for(int n, int prec, int tile_bits) {
+// Cluster tiles (opt-in with tile_bits = 16; complex64, 22 <= n <= 28): 2^16 indices over 8
+// CTAs, so two layouts hold every bit: [0,16) and [0, 32-n) + [16, n) (chunks of at least 16
+// amplitudes = 128 bytes).  On GB300 at n = 28 this is slower than three per-CTA layouts (the
+// 128-byte-chunk pass and the cluster barriers cost more than the saved pass), so it is not
+// the default.
+constexpr int kClusterTileBits = 16;
+bool cluster_layouts_apply(int n, int prec, int tile_bits) {
+  return prec == AQC_C64 && tile_bits == kClusterTileBits && n >= 22 && n <= 28;
+}
+
+std::vector<Layout> layouts_for(int n, int prec, int tile_bits, bool allow_clusters) {
   std::vector<Layout> ls;
-  const int tmax = tile_bits > 0 ? tile_bits : tile_bits_max(prec), cc = chunk_bits(prec);
+  if (allow_clusters && cluster_layouts_apply(n, prec, tile_bits)) {
+    const int T = tile_bits_max(prec) + kClusterBits;  // 16
+    ls.push_back(Layout{T, T, 0, T, kClusterBits});
+    ls.push_back(Layout{2 * T - n, T, n - T, T, kClusterBits});
+    return ls;
+  }
+  const int tmax = (tile_bits > 0 && tile_bits <= tile_bits_max(prec)) ? tile_bits : tile_bits_max(prec);
+  const int cc = chunk_bits(prec);
   if (n <= tmax) {
     ls.push_back(Layout{n, n, 0, n});
     return ls;
@@ -122,6 +139,7 @@ struct aqc_ctx {
   int64_t nsteps_req = 0;
   double kappa = 0.1;
   int tile_bits = 0;  // 0: the precision's default
+  bool in_batch = false;  // batch members use per-CTA tiles only
 
   bool have_state = false;
   bool hist_ready = false;
@@ -178,7 +196,7 @@ uint32_t compress_mask(const Layout& L, uint32_t x) {
   return r;
 }
 
-void plan_layouts(aqc_ctx* c) { c->layouts = layouts_for(c->n, c->prec, c->tile_bits); }
+void plan_layouts(aqc_ctx* c) { c->layouts = layouts_for(c->n, c->prec, c->tile_bits, !c->in_batch); }
 
 int build_tables(aqc_ctx* c) {
   plan_layouts(c);
@@ -368,8 +386,8 @@ int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, vo
     }
     p.dcode = (diag && c->table_class >= 0) ? c->d_dcode : nullptr;
     p.ntiles = 1u << (c->n - p.L.t);
-    const size_t smem = apply_smem_bytes(c->prec, p.L.t, c->nplain[l], c->ngeneral[l] + (first ? c->n_remote : 0),
-                                         diag ? c->n_z : 0);
+    const size_t smem = apply_smem_bytes(c->prec, p.L.t - p.L.cb, c->nplain[l],
+                                         c->ngeneral[l] + (first ? c->n_remote : 0), diag ? c->n_z : 0);
     if (smem > 227 * 1024) FAIL(c, AQC_E_UNSUPPORTED, "shared memory %zu bytes too large", smem);
     CUDA_TRY(c, launch_apply(c->prec, p, (int)smem, c->stream));
     c->launches++;
@@ -760,8 +778,9 @@ int aqc_set_schedule(aqc_ctx* ctx, int s_kind, double T, const double coefA[4], 
 int aqc_set_tile_bits(aqc_ctx* ctx, int tile_bits) {
   if (!ctx) return AQC_E_INVAL;
   const int lo = chunk_bits(ctx->prec) + 1, hi = tile_bits_max(ctx->prec);
-  if (tile_bits != 0 && (tile_bits < lo || tile_bits > hi))
-    FAIL(ctx, AQC_E_INVAL, "tile_bits must be 0 or in [%d, %d]", lo, hi);
+  const bool cluster = ctx->prec == AQC_C64 && tile_bits == kClusterTileBits;
+  if (tile_bits != 0 && !cluster && (tile_bits < lo || tile_bits > hi))
+    FAIL(ctx, AQC_E_INVAL, "tile_bits must be 0, in [%d, %d], or 16 (complex64 cluster tiles)", lo, hi);
   ctx->tile_bits = tile_bits;
   ctx->dirty = true;
   ctx->have_state = false;
@@ -1046,8 +1065,16 @@ int aqc_batch_add(aqc_batch* b, aqc_ctx* c, int* slot_out) {
     }
   if (slot < 0) BFAIL(b, AQC_E_NOMEM, "batch is full (%d members)", b->max_members);
   DeviceGuard dg(b->device);
+  if (!c->in_batch) {
+    c->in_batch = true;  // per-CTA tiles for the batched kernel
+    c->dirty = true;
+  }
   int rc = ensure_ready(c);
-  if (rc) BFAIL(b, rc, "member: %s", c->err.c_str());
+  if (rc) {
+    c->in_batch = false;
+    c->dirty = true;
+    BFAIL(b, rc, "member: %s", c->err.c_str());
+  }
   if (c->nsteps == 0) {
     c->nsteps = c->nsteps_req > 0 ? c->nsteps_req : rule_steps(c);
     c->h = c->T / (double)c->nsteps;
@@ -1093,6 +1120,8 @@ int aqc_batch_remove(aqc_batch* b, int slot) {
     BCUDA(b, cudaStreamSynchronize(b->stream));
   }
   b->members[slot] = nullptr;
+  c->in_batch = false;
+  c->dirty = true;
   memset(&b->h_insts[slot], 0, sizeof(BatchInst));
   BCUDA(b, cudaMemcpyAsync(b->d_insts + slot, &b->h_insts[slot], sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
   BCUDA(b, cudaStreamSynchronize(b->stream));

@@ -38,9 +38,14 @@ struct DevClass {  // clauses [begin, end) share group, penalty and scale
 };
 
 // Tile layout: tile bits are [0, c) and [h, h + w); t = c + w; remaining bits index tiles.
+// cb > 0: the tile belongs to a cluster of 2^cb CTAs; the top cb tile bits select the CTA, each
+// CTA holds 2^(t - cb) indices in its shared memory, and the others read it through
+// distributed shared memory.
 struct Layout {
   int c, h, w, t;
+  int cb;
 };
+constexpr int kClusterBits = 3;  // 8 CTAs per cluster
 
 struct DevTables {
   int n_layouts;

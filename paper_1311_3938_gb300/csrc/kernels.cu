@@ -13,11 +13,14 @@
 //    fused PEC step (Sec. I.B), Runge-Kutta stage, derivative, or energy.
 //  Reductions accumulate in FP64 per thread -> warp -> CTA -> last-CTA sum in fixed order,
 //  so results are bitwise reproducible.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
 #include "aqc_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace aqc {
 
@@ -202,7 +205,7 @@ __device__ __forceinline__ void load_coefficients(TileCtx<R>& T, const DevTables
                                                   int li, bool with_diag, bool with_remote, const uint8_t* dcode,
                                                   double w0, double w1, double w2, unsigned char* smem) {
   T.L = L;
-  T.tsize = 1u << L.t;
+  T.tsize = 1u << (L.t - L.cb);  // indices held by this CTA
   T.tmask = T.tsize - 1u;
   T.tab = tab;
   T.w0 = w0;
@@ -309,8 +312,22 @@ __device__ __forceinline__ void st16(C2* __restrict__ a, uint32_t i, const C2* v
 // One tile: stage the source tile in shared memory, then for every point of the tile compute
 // acc = q + diagonal + products, and run the mode epilogue.  rt0/rt1 collect the reduction
 // partials of this thread in the state precision.
-template <typename R, int MODE>
-__device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile, R& rt0, R& rt1) {
+template <bool CL>
+__device__ __forceinline__ void tile_sync() {
+  if (CL)
+    cg::this_cluster().sync();
+  else
+    __syncthreads();
+}
+
+// Shared memory of CTA `rank` of this cluster (this CTA's own for rank == own rank).
+template <typename C2>
+__device__ __forceinline__ const C2* cluster_smem(const C2* s, uint32_t rank) {
+  return cg::this_cluster().map_shared_rank(s, rank);
+}
+
+template <typename R, int MODE, bool CL>
+__device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile, uint32_t rank, R& rt0, R& rt1) {
   using C2 = typename Cplx<R>::T;
   constexpr int H = Blk<R>::H;
   constexpr int G = 2 * H;
@@ -325,26 +342,29 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
   C2* s_p = T.s_p;
 
   // stage the source tile with asynchronous 16-byte copies: a pair of consecutive indices for
-  // complex64 (tile bit 0 is global bit 0), one index for complex128
-  __syncthreads();  // readers of the previous tile (or of the coefficients' writers) are done
+  // complex64 (tile bit 0 is global bit 0), one index for complex128.  In a cluster this CTA
+  // stages the indices whose top tile bits equal its rank.
+  tile_sync<CL>();  // readers of the previous tile (or of the coefficients' writers) are done
   const uint32_t zb = tile_base(L, tile);
+  const uint32_t pbits = (uint32_t)(L.t - L.cb);
+  const uint32_t jbase = CL ? (rank << pbits) : 0u;
   const bool code_smem = T.tcls >= 0 && L.c >= 4 && tsize >= 16;
   {
     constexpr uint32_t per16 = 16 / sizeof(C2);  // indices per 16-byte granule
     const uint32_t granules = tsize / per16;
     for (uint32_t g = threadIdx.x; g < granules; g += blockDim.x) {
       const uint32_t j = g * per16;
-      cp_async16(s_p + j, src + tile_z(L, j, zb));
+      cp_async16(s_p + j, src + tile_z(L, jbase | j, zb));
     }
     if (code_smem) {  // the clause bytes of the tile, 16 contiguous indices per copy
       for (uint32_t g = threadIdx.x; g < (tsize >> 4); g += blockDim.x) {
         const uint32_t j = g << 4;
-        cp_async16(T.s_code + j, T.dcode + tile_z(L, j, zb));
+        cp_async16(T.s_code + j, T.dcode + tile_z(L, jbase | j, zb));
       }
     }
     cp_async_wait_all();
   }
-  __syncthreads();
+  tile_sync<CL>();  // every part of the tile is staged
 
   const bool full = tsize >= 2 * HB;  // every state with more than 6 (complex64) / 5 qubits
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -356,7 +376,7 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
     if (!full || itn * 2 * HB >= tsize) return;
 #pragma unroll
     for (int k = 0; k < 2; k++) {
-      const uint32_t zk = tile_z(L, (itn * 2 * HB + k * HB + lane * H) & tmask, zb);
+      const uint32_t zk = tile_z(L, jbase | ((itn * 2 * HB + k * HB + lane * H) & tmask), zb);
       if (T.qin) {
         C2 t[H];
         ld16<C2, H>(T.qin, zk, t);
@@ -383,12 +403,12 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
     uint32_t z[G];
 #pragma unroll
     for (int k = 0; k < 2; k++) {
-      zh[k] = tile_z(L, jh[k], zb);
+      zh[k] = tile_z(L, jbase | jh[k], zb);
 #pragma unroll
       for (int q = 0; q < H; q++) {
         const uint32_t jj = it * 2 * HB + k * HB + lane * H + q;
         ok[k * H + q] = jj < tsize;
-        z[k * H + q] = full ? zh[k] + q : tile_z(L, jj & tmask, zb);
+        z[k * H + q] = full ? zh[k] + q : tile_z(L, jbase | (jj & tmask), zb);
       }
     }
     // 1. pointwise global loads first; they complete while the shared-memory gathers run
@@ -473,21 +493,23 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
     // partner values u[g] = s(tile index of point g XOR lx); selects instead of runtime
     // indexing keep everything in registers
     auto gather = [&](uint32_t lx, C2 (&u)[G]) {
-      const uint32_t hi = lx & ~(HM | HB);
+      const uint32_t rk = lx >> pbits;  // cluster bits of the flip: partner CTA rank ^ rk
+      const uint32_t hi = lx & tmask & ~(HM | HB);
       const bool mh = (lx & HM) != 0, sw = (lx & HB) != 0;
       C2 part[G];
-      if (hi == 0) {
+      if (hi == 0 && rk == 0) {
 #pragma unroll
         for (int q = 0; q < H; q++) {
           part[q] = sw ? own[H + q] : own[q];
           part[H + q] = sw ? own[q] : own[H + q];
         }
       } else {
+        const C2* sp = (CL && rk) ? cluster_smem(s_p, rank ^ rk) : s_p;
         const uint32_t j0 = (sw ? jh[1] : jh[0]) ^ hi, j1 = (sw ? jh[0] : jh[1]) ^ hi;
         if (full) {
           C2 t0[H], t1[H];
-          ld16<C2, H>(s_p, j0, t0);
-          ld16<C2, H>(s_p, j1, t1);
+          ld16<C2, H>(sp, j0, t0);
+          ld16<C2, H>(sp, j1, t1);
 #pragma unroll
           for (int q = 0; q < H; q++) {
             part[q] = t0[q];
@@ -496,8 +518,8 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
         } else {
 #pragma unroll
           for (int q = 0; q < H; q++) {
-            part[q] = s_p[(j0 + q) & tmask];
-            part[H + q] = s_p[(j1 + q) & tmask];
+            part[q] = sp[(j0 + q) & tmask];
+            part[H + q] = sp[(j1 + q) & tmask];
           }
         }
       }
@@ -523,9 +545,11 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
     if (full) {
       for (int kk = 0; kk < T.npf; kk++) {
         const PFlip<R> f = T.s_pf[kk];
+        const uint32_t rk = f.lx >> pbits, lxl = f.lx & tmask;
+        const C2* sp = (CL && rk) ? cluster_smem(s_p, rank ^ rk) : s_p;
         C2 t0[H], t1[H];
-        ld16<C2, H>(s_p, jh[0] ^ f.lx, t0);
-        ld16<C2, H>(s_p, jh[1] ^ f.lx, t1);
+        ld16<C2, H>(sp, jh[0] ^ lxl, t0);
+        ld16<C2, H>(sp, jh[1] ^ lxl, t1);
 #pragma unroll
         for (int q = 0; q < H; q++) {
           ar[q] += f.c * t0[q].x;
@@ -671,7 +695,7 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
   }
 }
 
-template <typename R, int MODE>
+template <typename R, int MODE, bool CL>
 __global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
   using C2 = typename Cplx<R>::T;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -694,13 +718,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
   // reductions: per-thread partials over one tile in the state precision (a few dozen
   // points), promoted to FP64 once per tile; FP64 across tiles, CTAs and the grid
   double red[2] = {0.0, 0.0};
-  // persistent CTAs: one prologue and one reduction per CTA, tiles taken round-robin
-  for (uint32_t tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
+  // persistent CTAs (or clusters): one prologue and one reduction per CTA, tiles taken
+  // round-robin
+  uint32_t rank = 0, first = blockIdx.x, stride = gridDim.x;
+  if (CL) {
+    cg::cluster_group cl = cg::this_cluster();
+    rank = cl.block_rank();
+    first = blockIdx.x / cl.num_blocks();
+    stride = gridDim.x / cl.num_blocks();
+  }
+  for (uint32_t tile = first; tile < P.ntiles; tile += stride) {
     R rt0 = (R)0, rt1 = (R)0;
-    process_tile<R, MODE>(T, tile, rt0, rt1);
+    process_tile<R, MODE, CL>(T, tile, rank, rt0, rt1);
     red[0] += (double)rt0;
     red[1] += (double)rt1;
   }
+  if (CL) cg::this_cluster().sync();  // no CTA leaves while others may read its shared memory
 
   if (MODE == MODE_STEP || MODE == MODE_ENERGY) {
     if (grid_reduce<2>(red, P.partials, P.counter, T.s_red)) {
@@ -759,10 +792,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_batch(BatchLaunc
   T.acc = nullptr;
   R rt0 = (R)0, rt1 = (R)0;
   if (level > 0) {
-    process_tile<R, MODE_PARTIAL>(T, it.tile, rt0, rt1);
+    process_tile<R, MODE_PARTIAL, false>(T, it.tile, 0u, rt0, rt1);
     return;
   }
-  process_tile<R, MODE_STEP>(T, it.tile, rt0, rt1);
+  process_tile<R, MODE_STEP, false>(T, it.tile, 0u, rt0, rt1);
   double red[2] = {(double)rt0, (double)rt1};
   cta_reduce<2>(red, T.s_red);
   __shared__ int s_last;
@@ -798,60 +831,107 @@ size_t apply_smem_bytes(int prec, int t, int n_plain, int n_general, int n_z) {
                    : SmemMap<float>(tsize, n_plain, n_general, n_z).total;
 }
 
-// Persistent grid: (resident CTAs per SM for this smem size) x SMs, at most one CTA per tile.
-template <typename R, int MODE>
-static cudaError_t grid_for(uint32_t ntiles, int smem, int* grid) {
-  static int configured = 0, cached_smem = -1, cached_dev = -1, cached_sms = 0, cached_per = 0;
+// Persistent grid: (resident CTAs per SM for this smem size) x SMs, at most one CTA per tile;
+// for cluster layouts, the number of clusters that can be resident at once (x cluster size).
+template <typename R, int MODE, bool CL>
+static cudaError_t grid_for(uint32_t ntiles, int smem, cudaStream_t s, int* grid) {
+  static int configured = 0, cached_smem = -1, cached_dev = -1, cached_g = 0;
+  auto kern = k_apply<R, MODE, CL>;
   if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  int dev = 0, sms = 0, per = 0;
+  int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev == cached_dev && smem == cached_smem) {
-    sms = cached_sms;
-    per = cached_per;
-  } else {
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply<R, MODE>, kThreads, smem);
-    if (e != cudaSuccess) return e;
+  if (!(dev == cached_dev && smem == cached_smem)) {
+    int g = 0;
+    if (CL) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 1u << kClusterBits;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(1u << kClusterBits);
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+      if (e != cudaSuccess) return e;
+      g = (nclusters < 1 ? 1 : nclusters) << kClusterBits;
+    } else {
+      int sms = 0, per = 0;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem);
+      if (e != cudaSuccess) return e;
+      g = sms * (per < 1 ? 1 : per);
+    }
     cached_dev = dev;
     cached_smem = smem;
-    cached_sms = sms;
-    cached_per = per;
+    cached_g = g;
   }
-  if (per < 1) per = 1;
-  uint64_t g = (uint64_t)sms * (uint64_t)per;
+  uint64_t g = (uint64_t)cached_g;
   if (g > (uint64_t)kMaxApplyGrid) g = kMaxApplyGrid;
-  *grid = (int)(g < ntiles ? g : ntiles);
+  if (CL) {
+    const uint64_t tiles_ctas = (uint64_t)ntiles << kClusterBits;
+    if (g > tiles_ctas) g = tiles_ctas;
+    g &= ~(uint64_t)((1u << kClusterBits) - 1u);
+  } else if (g > ntiles) {
+    g = ntiles;
+  }
+  *grid = (int)g;
   return cudaSuccess;
 }
 
-template <typename R, int MODE>
+template <typename R, int MODE, bool CL>
 static cudaError_t launch_one(const ApplyParams& p, int smem, cudaStream_t s) {
   int grid = 0;
-  cudaError_t e = grid_for<R, MODE>(p.ntiles, smem, &grid);
+  cudaError_t e = grid_for<R, MODE, CL>(p.ntiles, smem, s, &grid);
   if (e != cudaSuccess) return e;
-  k_apply<R, MODE><<<grid, kThreads, smem, s>>>(p);
+  if (CL) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1u << kClusterBits;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_apply<R, MODE, CL>, p);
+    if (e != cudaSuccess) return e;
+  } else {
+    k_apply<R, MODE, CL><<<grid, kThreads, smem, s>>>(p);
+  }
   return cudaGetLastError();
 }
 
-template <typename R>
+template <typename R, bool CL>
 static cudaError_t launch_prec(const ApplyParams& p, int smem, cudaStream_t s) {
   switch (p.mode) {
-    case MODE_PARTIAL: return launch_one<R, MODE_PARTIAL>(p, smem, s);
-    case MODE_STEP: return launch_one<R, MODE_STEP>(p, smem, s);
-    case MODE_RK4: return launch_one<R, MODE_RK4>(p, smem, s);
-    case MODE_DERIV: return launch_one<R, MODE_DERIV>(p, smem, s);
-    case MODE_ENERGY: return launch_one<R, MODE_ENERGY>(p, smem, s);
+    case MODE_PARTIAL: return launch_one<R, MODE_PARTIAL, CL>(p, smem, s);
+    case MODE_STEP: return launch_one<R, MODE_STEP, CL>(p, smem, s);
+    case MODE_RK4: return launch_one<R, MODE_RK4, CL>(p, smem, s);
+    case MODE_DERIV: return launch_one<R, MODE_DERIV, CL>(p, smem, s);
+    case MODE_ENERGY: return launch_one<R, MODE_ENERGY, CL>(p, smem, s);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_apply(int prec, const ApplyParams& p, int smem, cudaStream_t s) {
-  return prec == 0 ? launch_prec<double>(p, smem, s) : launch_prec<float>(p, smem, s);
+  if (p.L.cb > 0) {
+    if (p.L.cb != kClusterBits || prec != 1) return cudaErrorInvalidValue;  // complex64 clusters only
+    return launch_prec<float, true>(p, smem, s);
+  }
+  return prec == 0 ? launch_prec<double, false>(p, smem, s) : launch_prec<float, false>(p, smem, s);
 }
 
 template <typename R, int NT>

@@ -45,7 +45,7 @@ class Context:
     # ---- lifetime
     def close(self):
         if getattr(self, "handle", None):
-            torch.cuda.synchronize(self.dev)
+            self.stream.synchronize()  # this context's work only, not the whole device
             N.aqc_destroy(self.handle)
             self.handle = None
             self.workspace = None

@@ -245,3 +245,46 @@ def test_error_codes():
         ctx.fidelity(1 << 6)
     assert e.value.code == N.AQC_E_INVAL
     ctx.close()
+
+
+@pytest.mark.parametrize("n", [22, 25])
+def test_cluster_tiles_match_cta_tiles_and_oracle(n):
+    """complex64 states of 22..28 qubits with 8-CTA cluster tiles (tile_bits = 16: two
+    layouts), the default per-CTA tiles and the oracle agree."""
+    H = O.Hamiltonian(n)
+    a = _ctx(n, C64)
+    a.set_tile_bits(16)
+    terms = random_terms(n, 4000 + n, nterms=28)
+    load_both(a, H, terms, random_clauses(n, 4000 + n, m=8))
+    b = _ctx(n, C64)
+    for g in range(3):
+        sel = [t for t in terms if t[0] == g]
+        if sel:
+            b.load_terms(g, [t[1] for t in sel], [t[2] for t in sel], [t[3] for t in sel])
+    for (g, bits, pen, scale) in random_clauses(n, 4000 + n, m=8):
+        b.load_clauses(g, [bits], penalty=pen, scale=scale)
+    poly = ((0.3, 0.2, -0.1, 0.05), (1.1, -0.4, 0.0, 0.2), (-0.7, 0.0, 0.5, 0.0))
+    for c in (a, b):
+        c.set_schedule(5.0, poly, 1)
+    psi = random_state(n, 7)
+    dpsi = torch.from_numpy(psi).cuda()
+    ga = a.hpsi(1.3, dpsi).cpu().numpy()
+    gb = b.hpsi(1.3, dpsi).cpu().numpy()
+    used = dpsi.to(torch.complex64).cpu().numpy().astype(np.complex128)
+    ref = O.hpsi(H, O.Schedule(5.0, 1, poly).weights(1.3), used, nthreads=16)
+    assert rel_err(ga, ref) < 3e-6 and rel_err(gb, ref) < 3e-6
+    assert rel_err(ga, gb) < 3e-6
+    a.close()
+    b.close()
+
+
+def test_cluster_tiles_propagation_n22():
+    """A propagation with cluster tiles (tile_bits = 16) matches the oracle."""
+    inst, ctx, H, sched = _setup_ec3(22, C64, 9, 5.0, nonlinear=True, s_kind=1)
+    ctx.set_tile_bits(16)
+    ctx.set_integrator(0, 0.0)
+    ctx.set_initial_state("uniform")
+    ctx.propagate(10)
+    ref = O.propagate(H, sched, O.step_count(H, sched), O.uniform_state(22), max_steps=10, nthreads=16)
+    assert rel_err(ctx.state(), ref.psi) < TOL_STATE[C64] * 0.1
+    ctx.close()
