@@ -246,7 +246,12 @@ def measure_serving(a):
         res = srv.serve(jobs)
     finally:
         srv.close()
-    res.pop("jobs")
+    done = res.pop("jobs")
+    # per-result fidelity error against the FP64 (complex128) path for the n <= 14 subset
+    W.attach_fp64_errors(done, max_n=14)
+    errs = [j.P1_err_fp64 for j in done if not math.isnan(j.P1_fp64)]
+    res["fp64_checked"] = len(errs)
+    res["max_P1_err_vs_fp64"] = max(errs) if errs else None
     res["workload"] = (f"{len(jobs)} requests, Poisson rate 8/s, n~U{{10..20}} + every 20th n=30, "
                        "path linear/nonlinear, T~U[2,20] (n=30: U[0.1,0.3]), complex64")
     return res

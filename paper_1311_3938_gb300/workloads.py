@@ -45,7 +45,13 @@ class Job:
     norm2: float = math.nan
     steps: int = 0
     route: str = ""
+    P1_fp64: float = math.nan  # the same job on the complex128 (FP64) path, if checked
     state: np.ndarray = field(default=None, repr=False)
+
+    @property
+    def P1_err_fp64(self):
+        """|P_1 - P_1(FP64)|: the fidelity error of this result against the FP64 path."""
+        return abs(self.P1 - self.P1_fp64)
 
     @property
     def latency(self):
@@ -163,6 +169,56 @@ def _nsteps(ctx, job):
     return ctx._nsteps
 
 
+def attach_fp64_errors(jobs, max_n=20, device=0):
+    """For complex64 results with n <= max_n, solve the same job on the complex128 (FP64)
+    path and store its P_1, so each result states its fidelity error against FP64."""
+    import copy
+
+    for job in jobs:
+        if job.precision != N.AQC_C64 or job.n > max_n or math.isnan(job.P1):
+            continue
+        ref = copy.deepcopy(job)
+        ref.precision = N.AQC_C128
+        ref.state = None
+        solve_single(ref, device)
+        job.P1_fp64 = ref.P1
+    return jobs
+
+
+def run_sweep_n20(seed=2, n=20, Ts=(10.0, 50.0, 200.0), device=0):
+    """The n = 20 workload: linear and nonlinear paths x s = t/T and smoothstep x T, in
+    complex128 and complex64; per run P_1, E, norm^2 - 1, grid steps, seconds, and the
+    complex64 fidelity error against the complex128 (FP64) result."""
+    rows = []
+    for nonlinear in (False, True):
+        for s_kind in (N.AQC_S_LINEAR, N.AQC_S_SMOOTHSTEP):
+            for T in Ts:
+                res = {}
+                for prec in (N.AQC_C128, N.AQC_C64):
+                    job = Job(jid=0, n=n, seed=seed, nonlinear=nonlinear, T=T, precision=prec, s_kind=s_kind)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    solve_single(job, device)
+                    torch.cuda.synchronize()
+                    res[prec] = (job, time.perf_counter() - t0)
+                j128, t128 = res[N.AQC_C128]
+                j64, t64 = res[N.AQC_C64]
+                rows.append({
+                    "path": "nonlinear" if nonlinear else "linear",
+                    "s": "smoothstep" if s_kind == N.AQC_S_SMOOTHSTEP else "t/T",
+                    "T": T,
+                    "grid_steps": j128.steps,
+                    "P1_c128": j128.P1,
+                    "E_c128": j128.E,
+                    "norm2_minus_1_c128": j128.norm2 - 1.0,
+                    "seconds_c128": t128,
+                    "P1_c64": j64.P1,
+                    "P1_err_c64_vs_fp64": abs(j64.P1 - j128.P1),
+                    "seconds_c64": t64,
+                })
+    return rows
+
+
 def run_sequential(jobs, device=0, keep_state=False):
     """Every job alone, one after another (the one-at-a-time baseline).  Returns wall seconds."""
     torch.cuda.synchronize()
@@ -171,6 +227,18 @@ def run_sequential(jobs, device=0, keep_state=False):
         solve_single(job, device, keep_state)
     torch.cuda.synchronize()
     return time.perf_counter() - t0
+
+
+def _main():
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="workload drivers")
+    ap.add_argument("what", choices=["sweep20"])
+    a = ap.parse_args()
+    if a.what == "sweep20":
+        for row in run_sweep_n20():
+            print(json.dumps(row), flush=True)
 
 
 class Server:
@@ -187,8 +255,12 @@ class Server:
         self.big_chunk = big_chunk
         self.keep_state = keep_state
         max_items = max_members * (1 << max(0, batch_max_n - 13 + 2)) + 1024
+        # the batch (many short jobs) runs on a high-priority stream, large jobs on low-priority
+        # streams, so CTAs of batch rounds are scheduled first whenever SMs free up
+        lo, hi = torch.cuda.Stream.priority_range()
+        self.hi_prio, self.lo_prio = hi, lo
         self.batch = Batch(precision, device=device, max_members=max_members, max_items=max_items, threads=threads,
-                           steps_per_round=steps_per_round)
+                           steps_per_round=steps_per_round, stream=torch.cuda.Stream(device, priority=hi))
         self.used = 0
         self.peak_used = 0
         self.occupancy = []
@@ -223,9 +295,9 @@ class Server:
                     slot = self.batch.add(ctx)
                     in_batch[slot] = (job, ctx, inst)
                 else:
-                    stream = torch.cuda.Stream(self.device)
+                    stream = torch.cuda.Stream(self.device, priority=self.lo_prio)
                     ctx, inst = make_context(job, self.device, stream=stream)
-                    big.append([job, ctx, inst, stream, None, 0])
+                    big.append([job, ctx, inst, stream, None, 0, []])
             prof["admit_s"] += time.perf_counter() - ta
             self.occupancy.append(self.used / max(1, self.budget))
             if not in_batch and not big:
@@ -238,14 +310,18 @@ class Server:
             if in_batch:
                 self.batch.run(1)
             for entry in big:
-                job, ctx, inst, stream, ev, enq = entry
-                if ev is None:
-                    with torch.cuda.stream(stream):
-                        ctx.propagate(self.big_chunk, stats=False)
+                job, ctx, inst, stream, ev, enq, inflight = entry
+                # at most two chunks of a large job in flight, so batch rounds interleave
+                while inflight and inflight[0].query():
+                    inflight.pop(0)
+                if ev is None and len(inflight) < 2:
+                    ctx.propagate(self.big_chunk, stats=False)
                     entry[5] = enq + self.big_chunk
+                    e = torch.cuda.Event()
+                    e.record(stream)
+                    inflight.append(e)
                     if entry[5] >= _nsteps(ctx, job):
-                        entry[4] = torch.cuda.Event()
-                        entry[4].record(stream)
+                        entry[4] = e
             prof["advance_s"] += time.perf_counter() - ta
             # retire finished work
             ta = time.perf_counter()
@@ -267,7 +343,7 @@ class Server:
                         del in_batch[slot]
                         done.append(job)
             for entry in list(big):
-                job, ctx, inst, stream, ev, enq = entry
+                job, ctx, inst, stream, ev, enq, inflight = entry
                 if ev is not None and ev.query():
                     job.steps = _nsteps(ctx, job)
                     job.route = "stream"
@@ -278,8 +354,16 @@ class Server:
                     big.remove(entry)
                     done.append(job)
             prof["retire_s"] += time.perf_counter() - ta
+            if not in_batch and big and all(len(e[6]) >= 2 or e[4] is not None for e in big):
+                time.sleep(2e-4)  # only large jobs in flight: do not spin
         wall = now()
         lat = np.array([j.latency for j in done]) if done else np.array([math.nan])
+        by_route = {}
+        for route in ("batch", "stream"):
+            lr = np.array([j.latency for j in done if j.route == route])
+            if lr.size:
+                by_route[route] = {"count": int(lr.size), "p50_latency_s": float(np.percentile(lr, 50)),
+                                   "p99_latency_s": float(np.percentile(lr, 99))}
         return {
             "completed": len(done),
             "wall_s": wall,
@@ -289,9 +373,14 @@ class Server:
             "hbm_budget_bytes": self.budget,
             "hbm_peak_bytes": self.peak_used,
             "hbm_mean_occupancy": float(np.mean(self.occupancy)) if self.occupancy else 0.0,
+            "by_route": by_route,
             "loop": prof,
             "jobs": done,
         }
 
     def close(self):
         self.batch.close()
+
+
+if __name__ == "__main__":
+    _main()
