@@ -696,7 +696,8 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
 }
 
 template <typename R, int MODE, bool CL>
-__global__ void __launch_bounds__(kThreads, 2) k_apply(const ApplyParams P) {
+__global__ void __launch_bounds__(kThreads, (MODE == MODE_PARTIAL && sizeof(R) == 4 && !CL) ? 3 : 2)
+    k_apply(const ApplyParams P) {
   using C2 = typename Cplx<R>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   TileCtx<R> T;
