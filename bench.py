@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--pec", type=int, default=PEC_DEFAULT, help="PEC steps per bench step")
     ap.add_argument("--n", type=int, default=N_QUBITS)
+    ap.add_argument("--slab-bits", type=int, default=0, help="slab order of the PEC step: 0 off, -1 auto")
     ap.add_argument("--no-c128", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -294,6 +295,7 @@ def run_ours(a):
         HB.load_ec3(ctx, inst)
         ctx.set_schedule(T_RUN, HB.linear_schedule())
         ctx.set_integrator(0, 0.0)
+        ctx.set_slab_bits(a.slab_bits)
         stream = ctx.stream
         pec_ms = []
         res = {}
@@ -414,7 +416,9 @@ def run_ours(a):
         },
         "roofline": {
             "bound": "hbm",
-            "kernel": "fused PEC step (k_apply partial layouts + MODE_STEP), per grid step",
+            "kernel": ("fused PEC step, per grid step: k_apply partial pass(es) + k_slab (last partial layout "
+                       "and step over L2-sized slabs)" if a.slab_bits != 0 else
+                       "fused PEC step, per grid step: k_apply partial layouts + MODE_STEP"),
             "achieved": r64["pec_step_gbs"],
             "peak": hbm_peak,
             "peak_kind": peak_kind,

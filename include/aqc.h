@@ -141,6 +141,20 @@ int aqc_get_grid(aqc_ctx *ctx, int64_t *n_steps, double *h);
  * Batch members always use per-CTA tiles.  Resets the integrator. */
 int aqc_set_tile_bits(aqc_ctx *ctx, int tile_bits);
 
+/* Slab order of a PEC step (one PEC step = the one H*psi evaluation of Sec. I.B plus the
+ * corrector/predictor update).  With three or more layouts, the last partial-sum pass and the
+ * fused step kernel run as one launch over slabs of the index space (fixed values of up to
+ * `slab_bits` index bits that neither layout holds): each slab's partial sum is consumed by
+ * the step while it is still in L2, so a step moves two state vectors less through HBM.
+ * 0 (default) = off, -1 = automatic (AQC_C64 states of 64 MiB or more, slabs of 2^20
+ * amplitudes), 1..11 = at most that many slab bits.  On GB300 the slab launch moves about 10%
+ * fewer bytes per step at 28 qubits but runs slower than the separate passes, hence off.  Results equal those of the layer order up
+ * to the rounding of the partial sums' summation order.  The step's CTAs wait for the partial
+ * tiles of their slab with a bounded poll; a wait that gives up (only possible after a fault
+ * elsewhere) makes the next aqc_propagate with stats return AQC_E_CUDA.  Does not reset the
+ * integrator. */
+int aqc_set_slab_bits(aqc_ctx *ctx, int slab_bits);
+
 /* Set psi(0) and reset the integrator to t = 0.  kind = AQC_INIT_*; `basis` for
  * AQC_INIT_BASIS; `user` points to 2^n interleaved amplitudes in the state precision. */
 int aqc_set_initial_state(aqc_ctx *ctx, int kind, uint64_t basis, const void *user);

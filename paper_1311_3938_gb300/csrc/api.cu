@@ -84,7 +84,7 @@ std::vector<Layout> layouts_for(int n, int prec, int tile_bits, bool allow_clust
 
 
 struct WsPlan {
-  size_t off_tab, off_slots, off_counter, off_partials, off_dcode, off_vec, vec_bytes, total;
+  size_t off_tab, off_slots, off_counter, off_sync, off_partials, off_dcode, off_vec, vec_bytes, total;
   size_t partial_doubles;
 };
 
@@ -94,7 +94,8 @@ WsPlan plan_workspace(int n, int prec) {
   w.off_tab = 0;
   w.off_slots = align_up(sizeof(DevTables), 256);
   w.off_counter = w.off_slots + 256;
-  w.off_partials = w.off_counter + 256;
+  w.off_sync = w.off_counter + 256;  // slab work counter + per-slab counters
+  w.off_partials = w.off_sync + align_up((1 + kMaxSlabs) * sizeof(unsigned), 256);
   // k_apply grids are persistent (at most kMaxApplyGrid CTAs); k_norm2 uses reduce_grid()
   size_t g = std::max((size_t)kMaxApplyGrid, (size_t)reduce_grid((uint64_t)1 << n));
   w.partial_doubles = 3 * g;
@@ -120,6 +121,7 @@ struct aqc_ctx {
   DevTables* d_tab = nullptr;
   double* d_slots = nullptr;
   unsigned* d_counter = nullptr;
+  unsigned* d_sync = nullptr;
   double* d_partials = nullptr;
   uint8_t* d_dcode = nullptr;
   DevTables* h_tab = nullptr;
@@ -139,6 +141,8 @@ struct aqc_ctx {
   int64_t nsteps_req = 0;
   double kappa = 0.1;
   int tile_bits = 0;  // 0: the precision's default
+  int slab_req = 0;   // slab bits: 0 off (default), -1 automatic, k > 0 at most k
+  SlabParams slab;    // slab-ordered last passes of a PEC step (slab.n_slabs == 0: off)
   bool in_batch = false;  // batch members use per-CTA tiles only
 
   bool have_state = false;
@@ -197,6 +201,56 @@ uint32_t compress_mask(const Layout& L, uint32_t x) {
 }
 
 void plan_layouts(aqc_ctx* c) { c->layouts = layouts_for(c->n, c->prec, c->tile_bits, !c->in_batch); }
+
+int popcount32(uint32_t v) { return __builtin_popcount(v); }
+
+// Slab order for the last two passes of a PEC step (SlabParams): needs three or more layouts
+// (one full partial pass carries the products no layout holds and reads nothing another slab
+// rewrites) and index bits outside layout 0 and the last layout.  "Automatic" selects it for
+// complex64 states larger than L2 (the step is HBM-bound there), with slabs of 2^20 indices;
+// the highest free bits are fixed, so a slab is made of the longest contiguous runs.  Off by
+// default: on GB300 at 28 qubits the single launch moves 10% fewer bytes than the separate
+// passes but runs slower (two CTAs per SM for both item kinds, more load latency exposed).
+void plan_slabs(aqc_ctx* c) {
+  memset(&c->slab, 0, sizeof(c->slab));
+  const int nl = (int)c->layouts.size();
+  if (c->slab_req == 0 || c->in_batch || nl < 3) return;
+  for (const Layout& L : c->layouts)
+    if (L.cb != 0) return;
+  const uint32_t all = c->n >= 32 ? 0xffffffffu : ((1u << c->n) - 1u);
+  const uint32_t avail = all & ~layout_mask(c->layouts[0]) & ~layout_mask(c->layouts[nl - 1]);
+  int want;
+  if (c->slab_req > 0) {
+    want = c->slab_req;
+  } else {
+    if (c->prec != AQC_C64 || c->N * c->amp < ((uint64_t)64 << 20)) return;
+    want = c->n - 20;
+  }
+  want = std::min(want, std::min(popcount32(avail), 11));
+  if (want <= 0) return;
+  uint32_t mask = 0;
+  for (int b = 31, got = 0; b >= 0 && got < want; b--) {
+    if ((avail >> b) & 1u) {
+      mask |= 1u << b;
+      got++;
+    }
+  }
+  SlabParams& S = c->slab;
+  S.slab_mask = mask;
+  S.free_part = all & ~layout_mask(c->layouts[nl - 1]) & ~mask;
+  S.free_step = all & ~layout_mask(c->layouts[0]) & ~mask;
+  S.n_slabs = 1u << want;
+  S.tiles = 1u << popcount32(S.free_step);
+  if (popcount32(S.free_part) != popcount32(S.free_step)) {  // layouts of unequal tile size
+    memset(&c->slab, 0, sizeof(c->slab));
+    return;
+  }
+  S.lookahead = std::min<uint32_t>(2u, S.n_slabs);
+  S.n_items = 2u * S.n_slabs * S.tiles;
+  S.spin_limit = 1u << 22;
+  S.queue = c->d_sync;
+  S.done = c->d_sync + 1;
+}
 
 int build_tables(aqc_ctx* c) {
   plan_layouts(c);
@@ -314,6 +368,7 @@ int build_tables(aqc_ctx* c) {
     c->launches++;
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  plan_slabs(c);
   c->dirty = false;
   return AQC_OK;
 }
@@ -365,11 +420,13 @@ ApplyParams base_params(aqc_ctx* c) {
 // (the first one also adds the products no layout holds); the contiguous layout 0 runs last
 // with the mode epilogue, so the kernel touching the most vectors has the smallest page
 // footprint per tile.  The diagonal is added by layout 0 (see diag_level).
-int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, void* partial_out) {
+// With top >= 0, only the partial passes of layouts top .. 1 run (the first of them adds the
+// products no layout holds); the caller finishes the evaluation.
+int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, void* partial_out, int top = -1) {
   const int nl = (int)c->layouts.size();
-  for (int step = 0; step < nl; step++) {
-    const int l = nl - 1 - step;
-    const bool first = (step == 0), last = (l == 0), diag = (l == diag_level(nl));
+  const int hi = top >= 0 ? top : nl - 1, lo = top >= 0 ? 1 : 0;
+  for (int l = hi; l >= lo; l--) {
+    const bool first = (l == hi), last = (l == 0), diag = (l == diag_level(nl));
     ApplyParams p = last ? fin : base_params(c);
     p.L = c->layouts[l];
     p.layout_index = l;
@@ -443,6 +500,43 @@ int start_history(aqc_ctx* c) {
   return AQC_OK;
 }
 
+// Slab order: layouts nl-2 .. 1 as full partial passes (the first adds the products no layout
+// holds), then one k_slab launch for layout nl-1 (partial) and layout 0 (fused step).
+int pec_step_slabs(aqc_ctx* c, const double w[3], const ApplyParams& fin) {
+  const int nl = (int)c->layouts.size();
+  ApplyParams stub = base_params(c);
+  stub.mode = MODE_PARTIAL;
+  stub.qout = c->vec[V_Q];
+  int rc = evaluate(c, w, c->vec[V_P], stub, c->vec[V_Q], nl - 2);
+  if (rc) return rc;
+  SlabParams S = c->slab;
+  const int lp = nl - 1;
+  S.part = base_params(c);
+  S.part.L = c->layouts[lp];
+  S.part.layout_index = lp;
+  S.part.mode = MODE_PARTIAL;
+  S.part.src = c->vec[V_P];
+  S.part.qin = c->vec[V_Q];
+  S.part.qout = c->vec[V_Q];
+  S.step = fin;
+  S.step.L = c->layouts[0];
+  S.step.layout_index = 0;
+  S.step.with_diag = (0 == diag_level(nl));
+  S.step.with_remote = 0;
+  S.step.src = c->vec[V_P];
+  S.step.qin = c->vec[V_Q];
+  S.step.dcode = (S.step.with_diag && c->table_class >= 0) ? c->d_dcode : nullptr;
+  for (int g = 0; g < 3; g++) S.part.w[g] = S.step.w[g] = w[g];
+  S.part.h = S.step.h = c->h;
+  const int t = c->layouts[0].t;
+  const size_t smem = apply_smem_bytes(c->prec, t, c->nplain[0], c->ngeneral[0], S.step.with_diag ? c->n_z : 0) +
+                      table_smem_bytes(c->prec, t, c->nplain[lp], c->ngeneral[lp], 0);
+  if (smem > 227 * 1024) FAIL(c, AQC_E_UNSUPPORTED, "shared memory %zu bytes too large", smem);
+  CUDA_TRY(c, launch_slab(c->prec, S, (int)smem, c->stream));
+  c->launches++;
+  return AQC_OK;
+}
+
 int pec_step(aqc_ctx* c) {
   const int64_t n = c->step;
   double w[3];
@@ -456,7 +550,7 @@ int pec_step(aqc_ctx* c) {
   fin.f2 = c->vec[V_F0 + (int)((n - 2) & 3)];
   fin.fout = c->vec[V_F0 + (int)((n + 1) & 3)];
   fin.pout = c->vec[V_P];
-  int rc = evaluate(c, w, c->vec[V_P], fin, nullptr);
+  int rc = c->slab.n_slabs ? pec_step_slabs(c, w, fin) : evaluate(c, w, c->vec[V_P], fin, nullptr);
   if (rc) return rc;
   c->evals++;
   c->step++;
@@ -685,13 +779,14 @@ int aqc_create(aqc_ctx** out, int device, int precision, int n_qubits, void* wor
   c->d_tab = (DevTables*)(c->ws + wp.off_tab);
   c->d_slots = (double*)(c->ws + wp.off_slots);
   c->d_counter = (unsigned*)(c->ws + wp.off_counter);
+  c->d_sync = (unsigned*)(c->ws + wp.off_sync);
   c->d_partials = (double*)(c->ws + wp.off_partials);
   c->d_dcode = (uint8_t*)(c->ws + wp.off_dcode);
   for (int v = 0; v < V_COUNT; v++) c->vec[v] = c->ws + wp.off_vec + (size_t)v * wp.vec_bytes;
   for (int g = 0; g < 3; g++)
     for (int k = 0; k < 4; k++) c->poly[g][k] = 0.0;
   DeviceGuard dg(device);
-  if (cudaMemsetAsync(c->ws + wp.off_slots, 0, 512, c->stream) != cudaSuccess ||
+  if (cudaMemsetAsync(c->ws + wp.off_slots, 0, wp.off_partials - wp.off_slots, c->stream) != cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess) {
     g_create_error = "cudaMemsetAsync on the workspace failed";
     delete c->h_tab;
@@ -784,6 +879,14 @@ int aqc_set_tile_bits(aqc_ctx* ctx, int tile_bits) {
   ctx->tile_bits = tile_bits;
   ctx->dirty = true;
   ctx->have_state = false;
+  return AQC_OK;
+}
+
+int aqc_set_slab_bits(aqc_ctx* ctx, int slab_bits) {
+  if (!ctx) return AQC_E_INVAL;
+  if (slab_bits < -1 || slab_bits > 11) FAIL(ctx, AQC_E_INVAL, "slab_bits must be -1, 0 or 1..11");
+  ctx->slab_req = slab_bits;
+  if (!ctx->dirty) plan_slabs(ctx);
   return AQC_OK;
 }
 
@@ -898,7 +1001,13 @@ int aqc_propagate(aqc_ctx* ctx, int64_t max_steps, aqc_stats* stats) {
         stats->max_err_est = sl[kSlotMaxErr];
         stats->last_err_est = sl[kSlotLastErr];
         stats->elapsed_ms = ms;
-        if (!isfinite(sl[kSlotNorm2])) {
+        if (sl[kSlotFault] != 0.0) {
+          ctx->err = "a slab-ordered step gave up waiting for its partial sums";
+          rc = AQC_E_CUDA;
+          const double zero = 0.0;
+          cudaMemcpyAsync(ctx->d_slots + kSlotFault, &zero, sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+          cudaStreamSynchronize(ctx->stream);
+        } else if (!isfinite(sl[kSlotNorm2])) {
           ctx->err = "non-finite state norm";
           rc = AQC_E_NUMERIC;
         }

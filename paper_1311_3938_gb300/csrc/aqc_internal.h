@@ -100,6 +100,29 @@ struct ApplyParams {
   double* slots;     // results: see kSlot*
 };
 
+// One PEC step's last two layout passes over slabs of the index space (kernel k_slab).  A slab
+// fixes the bits of slab_mask, bits that neither layout holds, so each slab is a union of
+// whole tiles of both layouts.  Work items run in the order P(0..D-1), then P(D+v), S(v) for
+// v = 0.., then the last S: P(s) = every tile of slab s of the partial layout (partial sum into
+// q), S(s) = every tile of slab s of layout 0 (the fused step); S(s) waits for P(s).  The q and
+// p of a slab are read again by S(s) shortly after P(s) wrote or read them, while they are still
+// in L2, so a step moves two vectors less from HBM than separate layout passes.
+struct SlabParams {
+  ApplyParams part;     // MODE_PARTIAL on the slab layout (src = p, qin = qout = q)
+  ApplyParams step;     // MODE_STEP on layout 0
+  uint32_t slab_mask;   // index bits fixed by a slab
+  uint32_t free_part;   // bits that number the partial layout's tiles within a slab
+  uint32_t free_step;   // the same for layout 0
+  uint32_t n_slabs;     // 2^popcount(slab_mask)
+  uint32_t tiles;       // tiles per slab (both layouts)
+  uint32_t lookahead;   // D, 1 <= D <= n_slabs
+  uint32_t n_items;     // 2 * n_slabs * tiles
+  uint32_t spin_limit;  // polls before a wait gives up (sets slots[kSlotFault])
+  unsigned* queue;      // next work item (reset to 0 by the last CTA)
+  unsigned* done;       // finished partial tiles per slab (reset to 0 by the last CTA)
+};
+constexpr int kMaxSlabs = 2048;
+
 // vectors of a state (workspace order)
 constexpr int kVecY = 0, kVecP = 1, kVecQ = 2, kVecF0 = 3, kVecAcc = 7, kVecCount = 8;
 
@@ -153,11 +176,14 @@ constexpr int kSlotMaxErr = 1;
 constexpr int kSlotLastErr = 2;
 constexpr int kSlotDot = 3;
 constexpr int kSlotDotIm = 4;
+constexpr int kSlotFault = 5;  // nonzero: an inter-CTA wait gave up (results of that step are invalid)
 constexpr int kSlotCount = 8;
 
 cudaError_t launch_apply(int prec, const ApplyParams& p, int smem_bytes, cudaStream_t s);
 int apply_grid(int prec, int mode, uint32_t ntiles, int smem_bytes);
 size_t apply_smem_bytes(int prec, int t, int n_plain, int n_general, int n_z);
+size_t table_smem_bytes(int prec, int t, int n_plain, int n_general, int n_z);
+cudaError_t launch_slab(int prec, const SlabParams& p, int smem_bytes, cudaStream_t s);
 cudaError_t launch_diag_codes(uint8_t* out, uint64_t N, const DevTables* tab, int cls, cudaStream_t s);
 cudaError_t launch_init(int prec, void* y, uint64_t N, int kind, uint64_t basis, cudaStream_t s);
 cudaError_t launch_predict(int prec, void* p, const void* y, const void* f3, const void* f2, const void* f1,

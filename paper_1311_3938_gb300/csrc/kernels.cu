@@ -171,6 +171,44 @@ __device__ __forceinline__ void cp_async16(void* smem_ptr, const void* gptr) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_ptr);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gptr) : "memory");
 }
+// The same with an L2 eviction-priority policy (createpolicy)
+__device__ __forceinline__ void cp_async16_pol(void* smem_ptr, const void* gptr, uint64_t pol) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_ptr);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gptr), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+// 16-byte global load / store with an L2 policy (loads bypass L1)
+__device__ __forceinline__ float4 ldg16_pol(const void* a, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;\n"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(a), "l"(pol)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void stg16_pol(void* a, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;\n" ::"l"(a), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w), "l"(pol)
+               : "memory");
+}
+// Drop a 128-byte L2 line without writing it back (its contents become undefined).  `dep` is a
+// value loaded from the line: the discard issues only after that load has returned.
+__device__ __forceinline__ void discard_l2(const void* a, float dep) {
+  asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(a), "f"(dep) : "memory");
+}
+__device__ __forceinline__ void discard_l2(const void* a, double dep) {
+  asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(a), "d"(dep) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -195,6 +233,7 @@ struct TileCtx {
   SFlip<R>* s_gf;
   SZ<R>* s_z;
   double* s_red;
+  uint64_t pol_keep, pol_drop;  // L2 policies (evict_last / evict_first) of hinted tile passes
 };
 
 __device__ __forceinline__ double pick3(double a, double b, double c, int g) { return g == 0 ? a : (g == 1 ? b : c); }
@@ -203,7 +242,8 @@ __device__ __forceinline__ double pick3(double a, double b, double c, int g) { r
 template <typename R>
 __device__ __forceinline__ void load_coefficients(TileCtx<R>& T, const DevTables* __restrict__ tab, const Layout& L,
                                                   int li, bool with_diag, bool with_remote, const uint8_t* dcode,
-                                                  double w0, double w1, double w2, unsigned char* smem) {
+                                                  double w0, double w1, double w2, unsigned char* smem,
+                                                  unsigned char* tables = nullptr) {
   T.L = L;
   T.tsize = 1u << (L.t - L.cb);  // indices held by this CTA
   T.tmask = T.tsize - 1u;
@@ -222,10 +262,13 @@ __device__ __forceinline__ void load_coefficients(TileCtx<R>& T, const DevTables
   const SmemMap<R> map(T.tsize, T.np, T.ng, T.nz);
   T.s_p = reinterpret_cast<typename TileCtx<R>::C2*>(smem);
   T.s_code = smem + map.code;
-  T.s_pf = reinterpret_cast<PFlip<R>*>(smem + map.pf);
-  T.s_gf = reinterpret_cast<SFlip<R>*>(smem + map.gf);
-  T.s_z = reinterpret_cast<SZ<R>*>(smem + map.zs);
-  T.s_red = reinterpret_cast<double*>(smem + map.red);
+  // coefficient tables after the tile, or in a region of their own (a second layout's tables
+  // in a kernel that runs tiles of two layouts)
+  unsigned char* tb = tables ? tables - map.pf : smem;
+  T.s_pf = reinterpret_cast<PFlip<R>*>(tb + map.pf);
+  T.s_gf = reinterpret_cast<SFlip<R>*>(tb + map.gf);
+  T.s_z = reinterpret_cast<SZ<R>*>(tb + map.zs);
+  T.s_red = reinterpret_cast<double*>(tb + map.red);
   for (int k = threadIdx.x; k < T.np; k += blockDim.x) {
     const DevFlip d = tab->flips[fb + k];
     PFlip<R> f;
@@ -300,6 +343,15 @@ __device__ __forceinline__ void ld16(const C2* __restrict__ a, uint32_t i, C2 (&
   for (int q = 0; q < H; q++) v[q] = xs[q];
 }
 
+// the same through L2 only: partial sums written by other CTAs of the same launch
+template <typename C2, int H>
+__device__ __forceinline__ void ld16cg(const C2* __restrict__ a, uint32_t i, C2 (&v)[H]) {
+  const float4 x = __ldcg(reinterpret_cast<const float4*>(a + i));
+  const C2* xs = reinterpret_cast<const C2*>(&x);
+#pragma unroll
+  for (int q = 0; q < H; q++) v[q] = xs[q];
+}
+
 template <typename C2, int H>
 __device__ __forceinline__ void st16(C2* __restrict__ a, uint32_t i, const C2* v) {
   float4 x;
@@ -307,6 +359,31 @@ __device__ __forceinline__ void st16(C2* __restrict__ a, uint32_t i, const C2* v
 #pragma unroll
   for (int q = 0; q < H; q++) xs[q] = v[q];
   *reinterpret_cast<float4*>(a + i) = x;
+}
+
+// Global 16-byte accesses of a tile pass.  HINT 0: plain; otherwise with an L2 policy.
+template <typename C2, int H, int HINT>
+__device__ __forceinline__ void gld16(const C2* __restrict__ a, uint32_t i, C2 (&v)[H], uint64_t pol) {
+  if (HINT) {
+    const float4 x = ldg16_pol(a + i, pol);
+    const C2* xs = reinterpret_cast<const C2*>(&x);
+#pragma unroll
+    for (int q = 0; q < H; q++) v[q] = xs[q];
+  } else {
+    ld16<C2, H>(a, i, v);
+  }
+}
+template <typename C2, int H, int HINT>
+__device__ __forceinline__ void gst16(C2* __restrict__ a, uint32_t i, const C2* v, uint64_t pol) {
+  if (HINT) {
+    float4 x;
+    C2* xs = reinterpret_cast<C2*>(&x);
+#pragma unroll
+    for (int q = 0; q < H; q++) xs[q] = v[q];
+    stg16_pol(a + i, x, pol);
+  } else {
+    st16<C2, H>(a, i, v);
+  }
 }
 
 // One tile: stage the source tile in shared memory, then for every point of the tile compute
@@ -326,8 +403,11 @@ __device__ __forceinline__ const C2* cluster_smem(const C2* s, uint32_t rank) {
   return cg::this_cluster().map_shared_rank(s, rank);
 }
 
-template <typename R, int MODE, bool CL>
-__device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile, uint32_t rank, R& rt0, R& rt1) {
+// HINT (L2 eviction priorities, full tiles only): 0 none; 1 a partial-sum pass whose source
+// tile and output are read again soon (kept), 2 a pass whose accesses are all last uses
+// (evicted first).
+template <typename R, int MODE, bool CL, int HINT = 0>
+__device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, uint32_t rank, R& rt0, R& rt1) {
   using C2 = typename Cplx<R>::T;
   constexpr int H = Blk<R>::H;
   constexpr int G = 2 * H;
@@ -345,7 +425,6 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
   // complex64 (tile bit 0 is global bit 0), one index for complex128.  In a cluster this CTA
   // stages the indices whose top tile bits equal its rank.
   tile_sync<CL>();  // readers of the previous tile (or of the coefficients' writers) are done
-  const uint32_t zb = tile_base(L, tile);
   const uint32_t pbits = (uint32_t)(L.t - L.cb);
   const uint32_t jbase = CL ? (rank << pbits) : 0u;
   const bool code_smem = T.tcls >= 0 && L.c >= 4 && tsize >= 16;
@@ -354,12 +433,18 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
     const uint32_t granules = tsize / per16;
     for (uint32_t g = threadIdx.x; g < granules; g += blockDim.x) {
       const uint32_t j = g * per16;
-      cp_async16(s_p + j, src + tile_z(L, jbase | j, zb));
+      if (HINT)
+        cp_async16_pol(s_p + j, src + tile_z(L, jbase | j, zb), HINT == 1 ? T.pol_keep : T.pol_drop);
+      else
+        cp_async16(s_p + j, src + tile_z(L, jbase | j, zb));
     }
     if (code_smem) {  // the clause bytes of the tile, 16 contiguous indices per copy
       for (uint32_t g = threadIdx.x; g < (tsize >> 4); g += blockDim.x) {
         const uint32_t j = g << 4;
-        cp_async16(T.s_code + j, T.dcode + tile_z(L, jbase | j, zb));
+        if (HINT)
+          cp_async16_pol(T.s_code + j, T.dcode + tile_z(L, jbase | j, zb), T.pol_drop);
+        else
+          cp_async16(T.s_code + j, T.dcode + tile_z(L, jbase | j, zb));
       }
     }
     cp_async_wait_all();
@@ -379,7 +464,10 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
       const uint32_t zk = tile_z(L, jbase | ((itn * 2 * HB + k * HB + lane * H) & tmask), zb);
       if (T.qin) {
         C2 t[H];
-        ld16<C2, H>(T.qin, zk, t);
+        if (HINT)
+          gld16<C2, H, HINT>(T.qin, zk, t, T.pol_drop);
+        else
+          ld16cg<C2, H>(T.qin, zk, t);
 #pragma unroll
         for (int q = 0; q < H; q++) pq[k * H + q] = t[q];
       }
@@ -431,18 +519,18 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
       for (int k = 0; k < 2; k++) {
         C2 t[H];
         if (kNeedY) {
-          ld16<C2, H>(T.y, zh[k], t);
+          gld16<C2, H, HINT>(T.y, zh[k], t, T.pol_drop);
 #pragma unroll
           for (int q = 0; q < H; q++) y0[k * H + q] = t[q];
         }
         if (kNeedF) {
-          ld16<C2, H>(T.f0, zh[k], t);
+          gld16<C2, H, HINT>(T.f0, zh[k], t, T.pol_drop);
 #pragma unroll
           for (int q = 0; q < H; q++) a[k * H + q] = t[q];
-          ld16<C2, H>(T.f1, zh[k], t);
+          gld16<C2, H, HINT>(T.f1, zh[k], t, T.pol_drop);
 #pragma unroll
           for (int q = 0; q < H; q++) b[k * H + q] = t[q];
-          ld16<C2, H>(T.f2, zh[k], t);
+          gld16<C2, H, HINT>(T.f2, zh[k], t, T.pol_drop);
 #pragma unroll
           for (int q = 0; q < H; q++) c[k * H + q] = t[q];
         } else if (MODE == MODE_RK4) {
@@ -456,7 +544,7 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
     } else {
 #pragma unroll
       for (int g = 0; g < G; g++) {
-        qv[g] = (T.qin && ok[g]) ? T.qin[z[g]] : zero2;
+        qv[g] = (T.qin && ok[g]) ? __ldcg(T.qin + z[g]) : zero2;
         if (kNeedY) y0[g] = ok[g] ? T.y[z[g]] : zero2;
         if (kNeedF) {
           a[g] = ok[g] ? T.f0[z[g]] : zero2;
@@ -612,6 +700,12 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
       ar[g] += qv[g].x;
       ai[g] += qv[g].y;
     }
+    // HINT 2: the partial sum is dead after this read; drop its L2 lines instead of writing
+    // them back (one lane per 128-byte line: eight lanes of 16 bytes)
+    if (HINT == 2 && full && T.qin && (lane & 7u) == 0u) {
+#pragma unroll
+      for (int k = 0; k < 2; k++) discard_l2(T.qin + zh[k], qv[k * H].x);
+    }
     // 5. epilogue
     const R h = T.h;
     const R h24 = h / (R)24;
@@ -679,9 +773,10 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t tile,
     if (full) {
 #pragma unroll
       for (int k = 0; k < 2; k++) {
-        if (d1) st16<C2, H>(d1, zh[k], o1 + k * H);
-        if (d2) st16<C2, H>(d2, zh[k], o2 + k * H);
-        if (d3) st16<C2, H>(d3, zh[k], o3 + k * H);
+        const uint64_t pol = HINT == 1 ? T.pol_keep : T.pol_drop;
+        if (d1) gst16<C2, H, HINT>(d1, zh[k], o1 + k * H, pol);
+        if (d2) gst16<C2, H, HINT>(d2, zh[k], o2 + k * H, pol);
+        if (d3) gst16<C2, H, HINT>(d3, zh[k], o3 + k * H, pol);
       }
     } else {
 #pragma unroll
@@ -730,7 +825,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_PARTIAL && sizeof(R) =
   }
   for (uint32_t tile = first; tile < P.ntiles; tile += stride) {
     R rt0 = (R)0, rt1 = (R)0;
-    process_tile<R, MODE, CL>(T, tile, rank, rt0, rt1);
+    process_tile<R, MODE, CL>(T, tile_base(T.L, tile), rank, rt0, rt1);
     red[0] += (double)rt0;
     red[1] += (double)rt1;
   }
@@ -748,6 +843,121 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_PARTIAL && sizeof(R) =
         P.slots[kSlotDotIm] = red[1];
       }
     }
+  }
+}
+
+// ---- slab-ordered step (last partial layout + fused step) ---------------------------------
+// bits of v deposited, lowest first, into the set bits of mask
+__device__ __forceinline__ uint32_t deposit_bits(uint32_t v, uint32_t mask) {
+  uint32_t r = 0u;
+  for (uint32_t m = mask; m != 0u && v != 0u; m &= m - 1u, v >>= 1) {
+    if (v & 1u) r |= m & (0u - m);
+  }
+  return r;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Work item -> (is the fused step, slab), see SlabParams.
+__device__ __forceinline__ void slab_item(const SlabParams& S, uint32_t block, bool& is_step, uint32_t& slab) {
+  const uint32_t D = S.lookahead, NS = S.n_slabs;
+  if (block < D) {
+    is_step = false;
+    slab = block;
+  } else if (block < D + 2u * (NS - D)) {
+    const uint32_t v = (block - D) >> 1;
+    is_step = ((block - D) & 1u) != 0u;
+    slab = is_step ? v : D + v;
+  } else {
+    is_step = true;
+    slab = NS - D + (block - D - 2u * (NS - D));
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 2) k_slab(const SlabParams S) {
+  using C2 = typename Cplx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t s_item;
+  TileCtx<R> TS, TP;
+  const ApplyParams& A = S.step;
+  const ApplyParams& B = S.part;
+  load_coefficients<R>(TS, A.tab, A.L, A.layout_index, A.with_diag != 0, A.with_remote != 0, A.dcode, A.w[0], A.w[1],
+                       A.w[2], smem);
+  const SmemMap<R> mapA(TS.tsize, TS.np, TS.ng, TS.nz);
+  load_coefficients<R>(TP, B.tab, B.L, B.layout_index, B.with_diag != 0, B.with_remote != 0, B.dcode, B.w[0], B.w[1],
+                       B.w[2], smem, smem + mapA.total);
+  TS.stage = TP.stage = 0;
+  TS.h = TP.h = (R)A.h;
+  TS.src = TP.src = reinterpret_cast<const C2*>(A.src);
+  TS.qin = reinterpret_cast<const C2*>(A.qin);
+  TS.y = reinterpret_cast<C2*>(A.y);
+  TS.f0 = reinterpret_cast<const C2*>(A.f0);
+  TS.f1 = reinterpret_cast<const C2*>(A.f1);
+  TS.f2 = reinterpret_cast<const C2*>(A.f2);
+  TS.fout = reinterpret_cast<C2*>(A.fout);
+  TS.pout = reinterpret_cast<C2*>(A.pout);
+  TS.qout = nullptr;
+  TS.acc = nullptr;
+  TP.qin = reinterpret_cast<const C2*>(B.qin);
+  TP.qout = reinterpret_cast<C2*>(B.qout);
+  TP.y = nullptr;
+  TP.f0 = TP.f1 = TP.f2 = nullptr;
+  TP.fout = TP.pout = TP.acc = nullptr;
+  TS.pol_keep = TP.pol_keep = policy_evict_last();
+  TS.pol_drop = TP.pol_drop = policy_evict_first();
+
+  double red[2] = {0.0, 0.0};
+  for (;;) {
+    __syncthreads();  // s_item of the previous item has been read by every thread
+    if (threadIdx.x == 0) s_item = atomicAdd(S.queue, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= S.n_items) break;
+    bool is_step;
+    uint32_t slab;
+    slab_item(S, item / S.tiles, is_step, slab);
+    const uint32_t j = item % S.tiles;
+    const uint32_t zs = deposit_bits(slab, S.slab_mask);
+    R rt0 = (R)0, rt1 = (R)0;
+    if (!is_step) {
+      process_tile<R, MODE_PARTIAL, false, 1>(TP, zs | deposit_bits(j, S.free_part), 0u, rt0, rt1);
+      __syncthreads();  // every thread's stores of this tile are issued
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(S.done + slab, 1u);
+      }
+    } else {
+      if (threadIdx.x == 0) {
+        // every partial tile of this slab was handed out earlier to a running CTA, so the wait
+        // ends; the poll limit only guards against a fault elsewhere
+        uint32_t polls = 0;
+        while (ld_acquire(S.done + slab) < S.tiles) {
+          if (++polls > S.spin_limit) {
+            A.slots[kSlotFault] = 1.0;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __syncthreads();
+      process_tile<R, MODE_STEP, false, 2>(TS, zs | deposit_bits(j, S.free_step), 0u, rt0, rt1);
+      red[0] += (double)rt0;
+      red[1] += (double)rt1;
+    }
+  }
+  if (grid_reduce<2>(red, A.partials, A.counter, TS.s_red)) {
+    A.slots[kSlotNorm2] = red[0];
+    const double e = (19.0 / 270.0) * sqrt(red[1]);
+    A.slots[kSlotLastErr] = e;
+    if (!(e <= A.slots[kSlotMaxErr])) A.slots[kSlotMaxErr] = e;
+    // every other CTA has left its item loop: reset the work counters for the next launch
+    *S.queue = 0u;
+    for (uint32_t k = 0; k < S.n_slabs; k++) S.done[k] = 0u;
   }
 }
 
@@ -793,10 +1003,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_batch(BatchLaunc
   T.acc = nullptr;
   R rt0 = (R)0, rt1 = (R)0;
   if (level > 0) {
-    process_tile<R, MODE_PARTIAL, false>(T, it.tile, 0u, rt0, rt1);
+    process_tile<R, MODE_PARTIAL, false>(T, tile_base(T.L, it.tile), 0u, rt0, rt1);
     return;
   }
-  process_tile<R, MODE_STEP, false>(T, it.tile, 0u, rt0, rt1);
+  process_tile<R, MODE_STEP, false>(T, tile_base(T.L, it.tile), 0u, rt0, rt1);
   double red[2] = {(double)rt0, (double)rt1};
   cta_reduce<2>(red, T.s_red);
   __shared__ int s_last;
@@ -933,6 +1143,50 @@ cudaError_t launch_apply(int prec, const ApplyParams& p, int smem, cudaStream_t 
     return launch_prec<float, true>(p, smem, s);
   }
   return prec == 0 ? launch_prec<double, false>(p, smem, s) : launch_prec<float, false>(p, smem, s);
+}
+
+size_t table_smem_bytes(int prec, int t, int n_plain, int n_general, int n_z) {
+  const uint32_t tsize = 1u << t;
+  if (prec == 0) {
+    const SmemMap<double> m(tsize, n_plain, n_general, n_z);
+    return m.total - m.pf;
+  }
+  const SmemMap<float> m(tsize, n_plain, n_general, n_z);
+  return m.total - m.pf;
+}
+
+template <typename R>
+static cudaError_t launch_slab_t(const SlabParams& p, int smem, cudaStream_t s) {
+  static int configured = 0, cached_smem = -1, cached_dev = -1, cached_g = 0;
+  auto kern = k_slab<R>;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (!(dev == cached_dev && smem == cached_smem)) {
+    int sms = 0, per = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    cached_dev = dev;
+    cached_smem = smem;
+    cached_g = sms * (per < 1 ? 1 : per);
+  }
+  int g = cached_g > kMaxApplyGrid ? kMaxApplyGrid : cached_g;
+  if ((uint32_t)g > p.n_items) g = (int)p.n_items;
+  kern<<<g, kThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slab(int prec, const SlabParams& p, int smem, cudaStream_t s) {
+  if (p.part.L.cb != 0 || p.step.L.cb != 0 || p.n_slabs == 0 || p.n_slabs > (uint32_t)kMaxSlabs || p.tiles == 0 ||
+      p.lookahead == 0 || p.lookahead > p.n_slabs)
+    return cudaErrorInvalidValue;
+  return prec == 0 ? launch_slab_t<double>(p, smem, s) : launch_slab_t<float>(p, smem, s);
 }
 
 template <typename R, int NT>

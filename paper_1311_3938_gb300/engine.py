@@ -89,6 +89,10 @@ class Context:
     def set_tile_bits(self, tile_bits=0):
         N.aqc_set_tile_bits(self.handle, tile_bits)
 
+    def set_slab_bits(self, slab_bits=0):
+        """Slab order of the PEC step: 0 off, -1 automatic, k > 0 at most k slab bits."""
+        N.aqc_set_slab_bits(self.handle, slab_bits)
+
     def set_integrator(self, n_steps=0, kappa=0.0):
         N.aqc_set_integrator(self.handle, n_steps, kappa)
 

@@ -288,3 +288,64 @@ def test_cluster_tiles_propagation_n22():
     ref = O.propagate(H, sched, O.step_count(H, sched), O.uniform_state(22), max_steps=10, nthreads=16)
     assert rel_err(ctx.state(), ref.psi) < TOL_STATE[C64] * 0.1
     ctx.close()
+
+
+# ------------------------------------------------------------------ slab-ordered PEC steps
+@pytest.mark.parametrize("prec", [C128, C64])
+@pytest.mark.parametrize("slab_bits", [1, 3, 6])
+def test_slab_order_random_terms_full_solve(prec, slab_bits):
+    """Slab order (last partial layout and fused step in one launch over slabs of the index
+    space) with small tiles: four layouts, so two full partial passes run first; random X/Y/Z
+    products (some held by no layout) and clauses; full solve against the oracle."""
+    n = 16
+    ctx = _ctx(n, prec)
+    ctx.set_tile_bits(8 if prec == C64 else 7)
+    ctx.set_slab_bits(slab_bits)
+    H = O.Hamiltonian(n)
+    terms = [(g, x, z, 0.3 * c) for (g, x, z, c) in random_terms(n, 91 + slab_bits, nterms=24)]
+    load_both(ctx, H, terms, random_clauses(n, 91 + slab_bits, m=6))
+    sched = O.Schedule(1.0, 0, ((1, -1, 0, 0), (0, 1, 0, 0), (0, 1, -1, 0)))
+    ctx.set_schedule(1.0, sched.poly, 0)
+    N = 40
+    ctx.set_integrator(N, 0.0)
+    psi0 = random_state(n, 5)
+    ctx.set_initial_state(psi0)
+    st = ctx.propagate(-1)
+    ref = O.propagate(H, sched, N, psi0, nthreads=8)
+    assert rel_err(ctx.state(), ref.psi) < TOL_STATE[prec]
+    ref_norm2 = float(np.vdot(ref.psi, ref.psi).real)
+    assert abs(st["norm2"] - ref_norm2) < (1e-12 if prec == C128 else 1e-5)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [C128, C64])
+def test_slab_order_matches_layer_order(prec):
+    """n = 23 EC3, nonlinear path: slab order (automatic for complex64 at this size, forced
+    for complex128) and layer order give the same state up to summation-order rounding, and
+    both match the oracle over the first 12 steps."""
+    n = 23
+    states = []
+    for slab in (-1 if prec == C64 else 3, 0):
+        inst, ctx, H, sched = _setup_ec3(n, prec, 6, 10.0, nonlinear=True, s_kind=1)
+        ctx.set_slab_bits(slab)
+        ctx.set_integrator(0, 0.0)
+        ctx.set_initial_state("uniform")
+        ctx.propagate(12)
+        states.append(ctx.state())
+        ctx.close()
+    assert rel_err(states[0], states[1]) < (1e-13 if prec == C128 else 1e-6)
+    ref = O.propagate(H, sched, O.step_count(H, sched), O.uniform_state(n), max_steps=12, nthreads=16)
+    assert rel_err(states[0], ref.psi) < TOL_STATE[prec] * 0.1
+
+
+def test_slab_bits_argument_checks():
+    from paper_1311_3938_gb300 import _native as N
+
+    ctx = _ctx(10, C64)
+    for bad in (-2, 12):
+        with pytest.raises(N.AqcError) as e:
+            ctx.set_slab_bits(bad)
+        assert e.value.code == N.AQC_E_INVAL
+    ctx.set_slab_bits(0)
+    ctx.set_slab_bits(-1)
+    ctx.close()
