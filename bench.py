@@ -78,9 +78,16 @@ def peaks():
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cu", "api.cu", "aqc_internal.h"):
+    for f in ("kernels.cu", "xpartial.cu", "api.cu", "aqc_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1311_3938_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def len_layouts(n, t, c):
+    """Number of tile layouts for n qubits (tile bits t, contiguous chunk bits c)."""
+    if n <= t:
+        return 1
+    return 1 + -(-(n - t) // (t - c))
 
 
 def profiled_traffic(prec_name):
@@ -329,6 +336,23 @@ def run_ours(a):
         launches = ctx.launch_count() - l0
         ms = e0.elapsed_time(e1)
         ms = max_over_ranks(ms)
+        # matvec only (aqc_hpsi: out = H(t) psi over all layout passes), device buffers
+        dt_state = torch.complex64 if amp == 8 else torch.complex128
+        mv_in = torch.full((1 << n,), 1.0 / math.sqrt(1 << n), dtype=dt_state, device=dev)
+        mv_out = torch.empty_like(mv_in)
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                ctx.hpsi(0.37 * T_RUN, mv_in, mv_out)
+            m0 = torch.cuda.Event(enable_timing=True)
+            m1 = torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            reps = 5
+            for _ in range(reps):
+                ctx.hpsi(0.37 * T_RUN, mv_in, mv_out)
+            m1.record(stream)
+        torch.cuda.synchronize()
+        mv_ms = m0.elapsed_time(m1) / reps
+        del mv_in, mv_out
         ab = alg_bytes(n, amp, a.pec)
         value = whole_job_value(ab, a.steps, world, ms)
         pec_step_ms = statistics.mean(pec_ms)
@@ -344,6 +368,7 @@ def run_ours(a):
             "t_end": res["st"]["t"],
             "launches": launches,
             "clocks": clocks,
+            "matvec_ms": mv_ms,
         }
         # end-to-end through the public API with host buffers
         if not a.no_e2e:
@@ -426,6 +451,15 @@ def run_ours(a):
             "frac": r64["pec_step_gbs"] / hbm_peak,
             "traffic": traffic,
             "alg_bytes_per_launch": 7 * (1 << n) * 8,
+        },
+        "matvec": {
+            "what": "aqc_hpsi: out = H(t) psi (all layout passes), device buffers",
+            "ms": r64["matvec_ms"],
+            "alg_bytes": 2 * (1 << n) * 8,
+            "achieved": 2 * (1 << n) * 8 / (r64["matvec_ms"] * 1e-3) / 1e9,
+            "unit": "GB/s",
+            "frac": 2 * (1 << n) * 8 / (r64["matvec_ms"] * 1e-3) / 1e9 / hbm_peak,
+            "moved_bytes_as_built": (3 * len_layouts(n, 13, 5) - 1) * (1 << n) * 8,
         },
         "cpu_baseline": cpu,
         "e2e": r64.get("e2e"),

@@ -1,5 +1,7 @@
 // C ABI (include/aqc.h): context, SQH term packing, layouts, schedule, step rule and the
 // integrator driver (RK4 start-up, then one fused PEC kernel chain per step).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -131,6 +133,7 @@ struct aqc_ctx {
   bool dirty = true;
   std::vector<Layout> layouts;
   std::vector<int> nplain, ngeneral;  // local X-string / general products per layout
+  std::vector<char> xpartial;        // layout l's partial pass can run as k_partial_x
   int n_remote = 0, n_z = 0;
   int table_class = -1;
 
@@ -294,6 +297,7 @@ int build_tables(aqc_ctx* c) {
   int pos = 0;
   c->nplain.assign(nl, 0);
   c->ngeneral.assign(nl, 0);
+  c->xpartial.assign(nl, 0);
   for (int l = 0; l <= nl; l++) {
     t->flip_begin[l] = pos;
     if (pos + (int)per[l].size() > kMaxFlips) FAIL(c, AQC_E_UNSUPPORTED, "more than %d off-diagonal products", kMaxFlips);
@@ -316,6 +320,12 @@ int build_tables(aqc_ctx* c) {
     if (l < nl) {
       c->nplain[l] = np;
       c->ngeneral[l] = (int)per[l].size() - np;
+    }
+    if (l > 0 && l < nl) {
+      bool ok = c->prec == AQC_C64 && xpartial_layout_ok(c->layouts[l]) && c->ngeneral[l] == 0 &&
+                xpartial_smem_bytes(np) <= 227 * 1024;
+      for (const DevFlip& f : per[l]) ok = ok && (f.lx & 1u) == 0u;  // pairs stay together
+      c->xpartial[l] = ok ? 1 : 0;
     }
     pos += (int)per[l].size();
   }
@@ -405,6 +415,36 @@ int64_t rule_steps(const aqc_ctx* c) {
   return std::max<int64_t>(4, (int64_t)n);
 }
 
+// The driver's tensor-map encoder, looked up once through the runtime (no link to libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// A complex64 vector of 2^n amplitudes as a 4-D float tensor whose box is one tile of layout L:
+// (2^(c+1) floats of the contiguous chunk, 2^(h-c) gap positions, 2^w tile rows, top bits).
+bool encode_tile_map(CUtensorMap* m, const void* v, int n, const Layout& L) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || ((uintptr_t)v & 15u)) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)2 << L.c, (cuuint64_t)1 << (L.h - L.c), (cuuint64_t)1 << L.w,
+                              (cuuint64_t)1 << (n - L.h - L.w)};
+  const cuuint64_t strides[3] = {(cuuint64_t)8 << L.c, (cuuint64_t)8 << L.h, (cuuint64_t)8 << (L.h + L.w)};
+  const cuuint32_t box[4] = {(cuuint32_t)2 << L.c, 1u, (cuuint32_t)1 << L.w, 1u};
+  const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(v), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 ApplyParams base_params(aqc_ctx* c) {
   ApplyParams p;
   memset(&p, 0, sizeof(p));
@@ -443,6 +483,24 @@ int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, vo
     }
     p.dcode = (diag && c->table_class >= 0) ? c->d_dcode : nullptr;
     p.ntiles = 1u << (c->n - p.L.t);
+    // X-string-only strided layouts: TMA-fed partial kernel
+    if (!last && !diag && c->xpartial[l] && !(first && c->n_remote > 0)) {
+      XPartialParams x;
+      memset(&x, 0, sizeof(x));
+      if (encode_tile_map(&x.tmap, src, c->n, p.L)) {
+        x.tab = c->d_tab;
+        x.L = p.L;
+        x.layout_index = l;
+        for (int g = 0; g < 3; g++) x.w[g] = w[g];
+        x.qin = p.qin;
+        x.qout = p.qout;
+        x.ntiles = p.ntiles;
+        x.slots = c->d_slots;
+        CUDA_TRY(c, launch_partial_x(x, (int)xpartial_smem_bytes(c->nplain[l]), c->stream));
+        c->launches++;
+        continue;
+      }
+    }
     const size_t smem = apply_smem_bytes(c->prec, p.L.t - p.L.cb, c->nplain[l],
                                          c->ngeneral[l] + (first ? c->n_remote : 0), diag ? c->n_z : 0);
     if (smem > 227 * 1024) FAIL(c, AQC_E_UNSUPPORTED, "shared memory %zu bytes too large", smem);
@@ -1002,7 +1060,7 @@ int aqc_propagate(aqc_ctx* ctx, int64_t max_steps, aqc_stats* stats) {
         stats->last_err_est = sl[kSlotLastErr];
         stats->elapsed_ms = ms;
         if (sl[kSlotFault] != 0.0) {
-          ctx->err = "a slab-ordered step gave up waiting for its partial sums";
+          ctx->err = "a kernel gave up waiting (a tile copy or a slab's partial sums); results are invalid";
           rc = AQC_E_CUDA;
           const double zero = 0.0;
           cudaMemcpyAsync(ctx->d_slots + kSlotFault, &zero, sizeof(double), cudaMemcpyHostToDevice, ctx->stream);

@@ -1,5 +1,6 @@
 // Internal declarations shared by the host driver (api.cu) and the kernels (kernels.cu).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -46,6 +47,20 @@ struct Layout {
   int cb;
 };
 constexpr int kClusterBits = 3;  // 8 CTAs per cluster
+
+// First index of tile b: b's low h-c bits go to index bits [c, h), the rest above h+w.
+__host__ __device__ __forceinline__ uint32_t tile_base(const Layout& L, uint32_t b) {
+  const uint32_t gap = (uint32_t)(L.h - L.c);
+  const uint32_t lowpart = b & ((1u << gap) - 1u);
+  const uint32_t hipart = gap >= 32 ? 0u : (b >> gap);
+  return (lowpart << L.c) | (hipart << (L.h + L.w));
+}
+
+// Index of tile position j (tile bits: [0,c) then [h,h+w)) in the tile starting at zb.
+__host__ __device__ __forceinline__ uint32_t tile_z(const Layout& L, uint32_t j, uint32_t zb) {
+  const uint32_t cm = (1u << L.c) - 1u;
+  return zb | (j & cm) | ((j >> L.c) << L.h);
+}
 
 struct DevTables {
   int n_layouts;
@@ -123,6 +138,21 @@ struct SlabParams {
 };
 constexpr int kMaxSlabs = 2048;
 
+// Partial-sum pass of a strided layout holding only X strings with real coefficients
+// (complex64, kernel k_partial_x): the source tile arrives by TMA through `tmap`.
+constexpr int kXTileBits = 13;
+struct XPartialParams {
+  CUtensorMap tmap;      // source as a 4-D float tensor (chunk, gap bits, tile rows, top bits)
+  const DevTables* tab;
+  Layout L;
+  int layout_index;
+  double w[3];
+  const void* qin;       // nullable
+  void* qout;
+  uint32_t ntiles;
+  double* slots;         // kSlotFault is set if a tile copy never completes
+};
+
 // vectors of a state (workspace order)
 constexpr int kVecY = 0, kVecP = 1, kVecQ = 2, kVecF0 = 3, kVecAcc = 7, kVecCount = 8;
 
@@ -184,6 +214,9 @@ int apply_grid(int prec, int mode, uint32_t ntiles, int smem_bytes);
 size_t apply_smem_bytes(int prec, int t, int n_plain, int n_general, int n_z);
 size_t table_smem_bytes(int prec, int t, int n_plain, int n_general, int n_z);
 cudaError_t launch_slab(int prec, const SlabParams& p, int smem_bytes, cudaStream_t s);
+bool xpartial_layout_ok(const Layout& L);
+size_t xpartial_smem_bytes(int n_flips);
+cudaError_t launch_partial_x(const XPartialParams& p, int smem_bytes, cudaStream_t s);
 cudaError_t launch_diag_codes(uint8_t* out, uint64_t N, const DevTables* tab, int cls, cudaStream_t s);
 cudaError_t launch_init(int prec, void* y, uint64_t N, int kind, uint64_t basis, cudaStream_t s);
 cudaError_t launch_predict(int prec, void* p, const void* y, const void* f3, const void* f2, const void* f1,

@@ -80,18 +80,6 @@ struct SmemMap {
   }
 };
 
-__device__ __forceinline__ uint32_t tile_base(const Layout& L, uint32_t b) {
-  const uint32_t gap = (uint32_t)(L.h - L.c);
-  const uint32_t lowpart = b & ((1u << gap) - 1u);
-  const uint32_t hipart = gap >= 32 ? 0u : (b >> gap);
-  return (lowpart << L.c) | (hipart << (L.h + L.w));
-}
-
-__device__ __forceinline__ uint32_t tile_z(const Layout& L, uint32_t j, uint32_t zb) {
-  const uint32_t cm = (1u << L.c) - 1u;
-  return zb | (j & cm) | ((j >> L.c) << L.h);
-}
-
 // warp + CTA reduction of K doubles in fixed order; result valid in thread 0
 template <int K>
 __device__ __forceinline__ void cta_reduce(double (&v)[K], double* s_red) {

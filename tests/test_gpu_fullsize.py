@@ -118,3 +118,40 @@ def test_n24_three_layouts_first_steps(prec):
     sched = O.nonlinear_path(T, 1)
     ref = O.propagate(H, sched, O.step_count(H, sched), O.uniform_state(n), max_steps=12, nthreads=16)
     assert rel_err(got, ref.psi) < TOL_STATE[prec] * 0.1
+
+
+@pytest.mark.parametrize("n", [22, 27])
+def test_x_string_partial_passes_sampled(n):
+    """Strided layouts holding only X strings run the TMA-fed partial kernel: single X on every
+    qubit, XX pairs inside one strided layout (some on its register-held tile bits, some not),
+    XX pairs spanning layouts (products no layout holds) and a diagonal; sampled outputs of
+    H(t) psi against the oracle's single-output evaluation."""
+    from paper_1311_3938_gb300.engine import Context
+
+    rng = np.random.default_rng(n)
+    terms = [(0, 1 << q, 0, float(rng.uniform(0.2, 1.0))) for q in range(n)]
+    for (a, b) in [(13, 14), (14, 16), (15, 20), (19, 20), (21, 22), (n - 1, n - 3), (n - 2, 21), (3, 25 % n),
+                   (0, 13), (6, n - 1), (17, n - 1)]:
+        if a != b and a < n and b < n:
+            terms.append((2, (1 << a) | (1 << b), 0, float(rng.uniform(-1.0, 1.0))))
+    terms.append((1, 0, (1 << 2) | (1 << (n - 1)), 0.7))
+    H = O.Hamiltonian(n)
+    ctx = Context(n, C64)
+    for g in range(3):
+        sel = [t for t in terms if t[0] == g]
+        if sel:
+            ctx.load_terms(g, [t[1] for t in sel], [t[2] for t in sel], [t[3] for t in sel])
+            for t in sel:
+                H.add_term(g, t[1], t[2], t[3])
+    poly = ((1, -1, 0, 0), (0, 1, 0, 0), (0, 1, -1, 0))
+    ctx.set_schedule(10.0, poly, 0)
+    psi = random_state(n, 99)
+    dpsi = torch.from_numpy(psi).to(torch.complex64).cuda()
+    out = ctx.hpsi(3.3, dpsi).cpu().numpy()
+    used = dpsi.cpu().numpy().astype(np.complex128)
+    del dpsi
+    ctx.close()
+    zs = _sample_indices(n, 1234, seed=n, count=3000)
+    ref = O.hpsi_at(H, O.Schedule(10.0, 0, poly).weights(3.3), used, zs)
+    got = out[zs.astype(np.int64)]
+    assert np.max(np.abs(got - ref)) < 2e-6 * np.abs(ref).max()
