@@ -8,6 +8,9 @@ Contents
       H_i = sum_i c_i (1 - sigma^x_i)                       (Eq. Hix; c_i = 1/2 or n_i/2)
       H_f = sum_clauses Omega * pen(#ones)                  (Eq. hci; or the Z/ZZ form Eq. final_ham)
       H_c = sum_(i,j) J_ij sigma^x_i sigma^x_j              (third path term, cf. Eq. nlpath)
+      H^xyz = Omega sum_{i<j} n_ij/2 (1 - sigma_i . sigma_j)  (Eq. Hixyz)
+      H^xy  = 3 m Omega 1 - Omega sum_{i<j} n_ij/2 (X_i X_j + Y_i Y_j)   (Eq. Hixy)
+  * `dicke_state`: the balanced superposition over one Hamming weight (Eq. initstate).
   * `hpsi` / `propagate`: thin ctypes calls into aqc_oracle.c (scatter-form SQH matvec, RK4
     start-up + Adams-Bashforth-Moulton-4 PEC integrator).
   * `dense_matrix`: explicit 2x2 Pauli matrices combined with Kronecker products, qubit 1 as
@@ -190,6 +193,58 @@ def add_xx_terms(H, pairs, group=2):
     """H_c = sum J_ij sigma^x_i sigma^x_j over the given (i, j, J) pairs."""
     for (i, j, J) in pairs:
         H.add_term(group, (1 << i) | (1 << j), 0, J)
+
+
+def clause_pair_counts(clauses):
+    """n_ij of Eq. final_ham: the number of clauses holding both bits i < j."""
+    nij = {}
+    for c in clauses:
+        b = sorted(c)
+        for x in range(3):
+            for y in range(x + 1, 3):
+                nij[(b[x], b[y])] = nij.get((b[x], b[y]), 0) + 1
+    return nij
+
+
+def add_xyz_driver(H, clauses, group=0, omega=1.0):
+    """Eq. Hixyz: Omega sum_{i<j} n_ij/2 (1 - X_i X_j - Y_i Y_j - Z_i Z_j) (Heisenberg ferromagnet
+    on the clause graph).  A Y on qubit q is written with both mask bits of q set."""
+    for (i, j), v in sorted(clause_pair_counts(clauses).items()):
+        m = (1 << i) | (1 << j)
+        a = omega * v / 2.0
+        H.add_term(group, 0, 0, a)
+        H.add_term(group, m, 0, -a)  # X_i X_j
+        H.add_term(group, m, m, -a)  # Y_i Y_j
+        H.add_term(group, 0, m, -a)  # Z_i Z_j
+
+
+def add_xy_driver(H, clauses, group=0, omega=1.0):
+    """Eq. Hixy: 3 m Omega 1 - Omega sum_{i<j} n_ij/2 (X_i X_j + Y_i Y_j)."""
+    H.add_term(group, 0, 0, 3.0 * len(clauses) * omega)
+    for (i, j), v in sorted(clause_pair_counts(clauses).items()):
+        m = (1 << i) | (1 << j)
+        H.add_term(group, m, 0, -omega * v / 2.0)
+        H.add_term(group, m, m, -omega * v / 2.0)
+
+
+def dicke_state(n, k):
+    """Eq. initstate: C(n, k)^{-1/2} times the sum of all basis states with k one-bits."""
+    N = 1 << n
+    w = np.array([bin(z).count("1") for z in range(N)])
+    psi = np.zeros(N, dtype=np.complex128)
+    psi[w == k] = 1.0 / math.sqrt(math.comb(n, k))
+    return psi
+
+
+def xy_hamiltonian(inst, driver="xy", penalty=PEN_INDICATOR, catalyst=None):
+    """The XY or XYZ algorithm (Sec. III.A.2-3): driver (group 0), H_f (group 1) and, with
+    `catalyst` = the list of kept clauses, H_{m-1} of Eq. nlpath as clauses in group 2."""
+    H = Hamiltonian(inst.n)
+    (add_xy_driver if driver == "xy" else add_xyz_driver)(H, inst.clauses, 0)
+    add_ec3_clauses(H, inst.clauses, 1, penalty)
+    if catalyst is not None:
+        add_ec3_clauses(H, catalyst, 2, penalty)
+    return H
 
 
 def ec3_hamiltonian(inst, penalty=PEN_INDICATOR, pairs=None, x_weights=None):

@@ -1,0 +1,106 @@
+"""Pins of the oracle's XY / XYZ algorithms (Sec. III.A.2-3) against mathematics.
+
+* Eq. Hixyz and Eq. Hixy on basis states: sigma_i . sigma_j |z> = zeta |z> + 2 [z_i != z_j] |z'>
+  (zeta = +1 for equal bits, -1 otherwise; z' swaps bits i and j), so
+      H^xyz |z> = sum_{i<j, z_i != z_j} n_ij (|z> - |z'>)
+      H^xy  |z> = 3 m |z> - sum_{i<j, z_i != z_j} n_ij |z'>
+  by brute force over all basis states (a wrong Y sign or a dropped term breaks it).
+* The Dicke state of every weight is a zero-energy (ground) state of H^xyz (Eq. initstate):
+  the symmetric states are pair triplets, where sigma_i . sigma_j = 1.
+* Hamming weight is a constant of motion (Eq. Sigmaz): the XY and XYZ paths keep amplitudes
+  outside the start sector exactly zero.
+* The XYZ algorithm started in the Dicke state of the solution's weight reaches the solution
+  at large T, with the energy bound of Sec. II.B.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from instances import generate_ec3
+from oracle import oracle as O
+
+
+def _basis(n, z):
+    v = np.zeros(1 << n, dtype=np.complex128)
+    v[z] = 1.0
+    return v
+
+
+def _swap(z, i, j):
+    return z ^ ((1 << i) | (1 << j))
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_drivers_on_basis_states(seed):
+    inst = generate_ec3(7, seed)
+    n, m = inst.n, inst.m
+    nij = {}
+    for c in inst.clauses:  # counted here by hand, independently of the oracle's helper
+        for a in c:
+            for b in c:
+                if a < b:
+                    nij[(a, b)] = nij.get((a, b), 0) + 1
+    Hxyz = O.Hamiltonian(n)
+    O.add_xyz_driver(Hxyz, inst.clauses, 0)
+    Hxy = O.Hamiltonian(n)
+    O.add_xy_driver(Hxy, inst.clauses, 0)
+    for z in range(1 << n):
+        e_xyz = np.zeros(1 << n, dtype=np.complex128)
+        e_xy = np.zeros(1 << n, dtype=np.complex128)
+        e_xy[z] += 3 * m
+        for (i, j), v in nij.items():
+            if ((z >> i) & 1) != ((z >> j) & 1):
+                e_xyz[z] += v
+                e_xyz[_swap(z, i, j)] -= v
+                e_xy[_swap(z, i, j)] -= v
+        got_xyz = O.hpsi(Hxyz, [1.0, 0.0, 0.0], _basis(n, z))
+        got_xy = O.hpsi(Hxy, [1.0, 0.0, 0.0], _basis(n, z))
+        assert np.max(np.abs(got_xyz - e_xyz)) < 1e-13
+        assert np.max(np.abs(got_xy - e_xy)) < 1e-13
+
+
+def test_dicke_states_are_xyz_ground_states():
+    inst = generate_ec3(8, 3)
+    n = inst.n
+    H = O.Hamiltonian(n)
+    O.add_xyz_driver(H, inst.clauses, 0)
+    for k in range(n + 1):
+        d = O.dicke_state(n, k)
+        assert abs(np.vdot(d, d).real - 1.0) < 1e-14
+        w = np.array([bin(z).count("1") for z in range(1 << n)])
+        assert np.all(d[w != k] == 0) and np.all(d[w == k].real > 0)
+        assert np.max(np.abs(O.hpsi(H, [1.0, 0.0, 0.0], d))) < 1e-12
+    # and zero is the bottom of the spectrum: 1 - sigma_i . sigma_j >= 0
+    ev = np.linalg.eigvalsh(O.dense_matrix(H, [1.0, 0.0, 0.0]))
+    assert abs(ev[0]) < 1e-10
+
+
+@pytest.mark.parametrize("driver", ["xy", "xyz"])
+def test_paths_conserve_hamming_weight(driver):
+    inst = generate_ec3(8, 4)
+    n = inst.n
+    k = bin(inst.solution).count("1")
+    keep = list(inst.clauses[:-1])
+    H = O.xy_hamiltonian(inst, driver=driver, catalyst=keep)
+    sched = O.nonlinear_path(3.0, alpha=8.0)
+    res = O.propagate(H, sched, O.step_count(H, sched), O.dicke_state(n, k))
+    w = np.array([bin(z).count("1") for z in range(1 << n)])
+    assert np.all(res.psi[w != k] == 0)
+    assert abs(np.vdot(res.psi, res.psi).real - 1.0) < 1e-5
+
+
+def test_xyz_algorithm_adiabatic_limit():
+    inst = generate_ec3(7, 5)
+    n = inst.n
+    k = bin(inst.solution).count("1")
+    H = O.xy_hamiltonian(inst, driver="xyz")
+    P1 = []
+    for T in (5.0, 80.0):
+        sched = O.linear_path(T)
+        res = O.propagate(H, sched, O.step_count(H, sched), O.dicke_state(n, k))
+        p1 = O.fidelity(res.psi, inst.solution)
+        E = O.energy(H, res.psi, 1)
+        assert E >= (1.0 - p1) - 1e-9  # Sec. II.B: every excited state costs at least Omega
+        P1.append(p1)
+    assert P1[1] > 0.9 and P1[1] > P1[0]
