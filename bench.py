@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-xy", action="store_true")
     ap.add_argument("--batch-count", type=int, default=48)
     ap.add_argument("--serve-count", type=int, default=40)
     return ap.parse_args()
@@ -241,6 +242,37 @@ def measure_batched(a):
     }
 
 
+def measure_xy(a, n=24, seed=3, pec=48):
+    """PEC step of the XY algorithm with the alpha = 8 catalyst (Eq. Hixy, Eq. nlpath) from the
+    Dicke state: Y products run through the general-product loop, pairs across layouts through
+    the remote gather, so it moves more than the X-driver step."""
+    import torch
+
+    from instances import generate_ec3
+    from paper_1311_3938_gb300 import hamiltonians as HB
+    from paper_1311_3938_gb300.engine import Context
+    import paper_1311_3938_gb300 as P
+
+    inst = generate_ec3(n, seed)
+    ctx = Context(n, P.AQC_C64)
+    sched, k = HB.load_xy(ctx, inst, driver="xy", catalyst_alpha=8.0)
+    ctx.set_schedule(20.0, sched)
+    ctx.set_integrator(0, 0.0)
+    ctx.set_initial_state(("dicke", k))
+    ctx.propagate(4, stats=False)
+    ms = []
+    for _ in range(3):
+        st = ctx.propagate(pec, stats=True)
+        ms.append(st["elapsed_ms"] / pec)
+    torch.cuda.synchronize()
+    ctx.close()
+    step_ms = min(ms)
+    gbs = 7 * (1 << n) * 8 / (step_ms * 1e-3) / 1e9
+    return {"workload": f"XY algorithm + catalyst, EC3 n={n} seed {seed}, T=20, Dicke start, complex64",
+            "pec_step_ms": step_ms, "achieved": gbs, "unit": "GB/s (7 N b per PEC step)",
+            "frac": gbs / peaks()[0]}
+
+
 def measure_serving(a):
     """Continuous batching of a seeded Poisson stream (rate 8/s): n ~ U{10..20} with every
     20th job n = 30 (64 GiB workspace), linear/nonlinear uniform, T ~ U[2, 20] (n = 30:
@@ -407,6 +439,7 @@ def run_ours(a):
     r128 = None if a.no_c128 else measure(P.AQC_C128)
     batched = None if (a.no_batch or world > 1) else measure_batched(a)
     serving = None if (a.no_serve or world > 1) else measure_serving(a)
+    xy = None if (a.no_xy or world > 1) else measure_xy(a)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         gbs, cores, desc, _ = cpu_sample()
@@ -468,6 +501,7 @@ def run_ours(a):
         "fidelity_P1_window": r64["P1"],
         "batched": batched,
         "serving": serving,
+        "xy_algorithm": xy,
     }
     if r128 is not None:
         flops = pec_flops_c128(n) * (1 << n)

@@ -62,6 +62,7 @@ extern "C" {
 #define AQC_INIT_BASIS 1       /* |basis>                                                 */
 #define AQC_INIT_USER_HOST 2   /* copy of a host vector (state precision, interleaved)   */
 #define AQC_INIT_USER_DEVICE 3 /* copy of a device vector (state precision, interleaved) */
+#define AQC_INIT_DICKE 4       /* C(n,k)^{-1/2} sum_{|u|=k} |u>, k = `basis` (Eq. initstate)  */
 
 typedef struct aqc_ctx aqc_ctx;
 
@@ -155,8 +156,11 @@ int aqc_set_tile_bits(aqc_ctx *ctx, int tile_bits);
  * integrator. */
 int aqc_set_slab_bits(aqc_ctx *ctx, int slab_bits);
 
-/* Set psi(0) and reset the integrator to t = 0.  kind = AQC_INIT_*; `basis` for
- * AQC_INIT_BASIS; `user` points to 2^n interleaved amplitudes in the state precision. */
+/* Set psi(0) and reset the integrator to t = 0.  kind = AQC_INIT_*; `basis` is the index for
+ * AQC_INIT_BASIS and the Hamming weight k (0..n) for AQC_INIT_DICKE (the balanced superposition
+ * of all basis states with k one-bits, the ground state of Eq. Hixyz in that sector);
+ * `user` points to 2^n interleaved amplitudes in the state precision (host or device memory
+ * per the kind).  Out-of-range index or weight: AQC_E_INVAL. */
 int aqc_set_initial_state(aqc_ctx *ctx, int kind, uint64_t basis, const void *user);
 
 /* Advance by up to max_steps grid steps (max_steps < 0: to t = T).  The first three steps

@@ -292,7 +292,20 @@ int build_tables(aqc_ctx* c) {
       }
     }
     f.lx = where < nl ? compress_mask(c->layouts[where], th.x) : 0u;
-    per[where].push_back(f);
+    // a second product with the same flip mask shares the first one's gather
+    bool merged = false;
+    for (DevFlip& e : per[where]) {
+      if (e.x == f.x && !e.has2) {
+        e.has2 = 1;
+        e.zm2 = f.zm;
+        e.group2 = f.group;
+        e.ipow2 = f.ipow;
+        e.coef2 = f.coef;
+        merged = true;
+        break;
+      }
+    }
+    if (!merged) per[where].push_back(f);
   }
   int pos = 0;
   c->nplain.assign(nl, 0);
@@ -307,14 +320,14 @@ int build_tables(aqc_ctx* c) {
     if (l < nl) {
       const uint32_t regbits = c->prec == AQC_C128 ? kRegBitsC128 : kRegBitsC64;
       for (const DevFlip& f : per[l])
-        if (f.zm == 0 && (f.lx & regbits) == 0) t->flips[pos + np++] = f;
+        if (f.zm == 0 && !f.has2 && (f.lx & regbits) == 0) t->flips[pos + np++] = f;
       nfast = np;
       for (const DevFlip& f : per[l])
-        if (f.zm == 0 && (f.lx & regbits) != 0) t->flips[pos + np++] = f;
+        if (f.zm == 0 && !f.has2 && (f.lx & regbits) != 0) t->flips[pos + np++] = f;
     }
     int k = np;
     for (const DevFlip& f : per[l])
-      if (l == nl || f.zm != 0) t->flips[pos + k++] = f;
+      if (l == nl || f.zm != 0 || f.has2) t->flips[pos + k++] = f;
     t->plain_count[l] = np;
     t->plain_fast[l] = nfast;
     if (l < nl) {
@@ -974,14 +987,22 @@ int aqc_set_initial_state(aqc_ctx* ctx, int kind, uint64_t basis, const void* us
   const size_t bytes = (size_t)ctx->N * ctx->amp;
   switch (kind) {
     case AQC_INIT_UNIFORM:
-      CUDA_TRY(ctx, launch_init(ctx->prec, y, ctx->N, 0, 0, ctx->stream));
+      CUDA_TRY(ctx, launch_init(ctx->prec, y, ctx->N, 0, 0, 0.0, ctx->stream));
       ctx->launches++;
       break;
     case AQC_INIT_BASIS:
       if (basis >= ctx->N) FAIL(ctx, AQC_E_INVAL, "basis index >= 2^n");
-      CUDA_TRY(ctx, launch_init(ctx->prec, y, ctx->N, 1, basis, ctx->stream));
+      CUDA_TRY(ctx, launch_init(ctx->prec, y, ctx->N, 1, basis, 0.0, ctx->stream));
       ctx->launches++;
       break;
+    case AQC_INIT_DICKE: {
+      if (basis > (uint64_t)ctx->n) FAIL(ctx, AQC_E_INVAL, "Hamming weight %llu > n", (unsigned long long)basis);
+      double binom = 1.0;  // C(n, k), exact in FP64 for n <= 31
+      for (uint64_t i = 1; i <= basis; i++) binom = binom * (double)(ctx->n - basis + i) / (double)i;
+      CUDA_TRY(ctx, launch_init(ctx->prec, y, ctx->N, 2, basis, 1.0 / sqrt(binom), ctx->stream));
+      ctx->launches++;
+      break;
+    }
     case AQC_INIT_USER_HOST:
       if (!user) FAIL(ctx, AQC_E_INVAL, "user vector is NULL");
       CUDA_TRY(ctx, cudaMemcpyAsync(y, user, bytes, cudaMemcpyHostToDevice, ctx->stream));

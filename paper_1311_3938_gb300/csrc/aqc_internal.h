@@ -14,15 +14,22 @@ constexpr int kMaxLayouts = 8;
 constexpr int kMaxN = 31;
 constexpr int kMaxApplyGrid = 4096;  // persistent k_apply grids never exceed this many CTAs
 
-// One off-diagonal Pauli product in gather form: (P psi)(z) = i^ipow (-1)^{|zm & (z^x)|} psi(z^x).
+// One off-diagonal Pauli product in gather form: (P psi)(z) = i^ipow (-1)^{|zm & (z^x)|} psi(z^x),
+// optionally with a companion product of the same flip mask x (zm2, ipow2, group2, coef2) that
+// shares the gather: X_iX_j + Y_iY_j of Eq. Hixy is one entry whose coefficient is exactly
+// 2c or 0 per source index, so Hamming-weight sectors stay exactly separate.
 struct DevFlip {
   uint32_t x;      // global flip mask
   uint32_t lx;     // the same mask in tile-local bits of its layout (0 for remote terms)
   uint32_t zm;     // Z/Y positions (sign from the source index z^x)
+  uint32_t zm2;    // companion's Z/Y positions
   int32_t group;   // weight slot A/B/C
   int32_t ipow;    // |x & zm| mod 4 (Y = i X Z)
+  int32_t group2, ipow2;
+  int32_t has2;    // a companion product is present
   int32_t pad;
   double coef;
+  double coef2;
 };
 
 struct DevZ {      // diagonal product coef (-1)^{|zm & z|}
@@ -218,7 +225,7 @@ bool xpartial_layout_ok(const Layout& L);
 size_t xpartial_smem_bytes(int n_flips);
 cudaError_t launch_partial_x(const XPartialParams& p, int smem_bytes, cudaStream_t s);
 cudaError_t launch_diag_codes(uint8_t* out, uint64_t N, const DevTables* tab, int cls, cudaStream_t s);
-cudaError_t launch_init(int prec, void* y, uint64_t N, int kind, uint64_t basis, cudaStream_t s);
+cudaError_t launch_init(int prec, void* y, uint64_t N, int kind, uint64_t basis, double amp, cudaStream_t s);
 cudaError_t launch_predict(int prec, void* p, const void* y, const void* f3, const void* f2, const void* f1,
                            const void* f0, double h, uint64_t N, cudaStream_t s);
 cudaError_t launch_reduce(int prec, int what, const void* a, uint64_t N, double* partials, unsigned* counter,

@@ -37,8 +37,9 @@ struct Cplx<double> {
 
 template <typename R>
 struct SFlip {
-  uint32_t lx, x, zm, cplx;  // cplx: coefficient has an imaginary part (odd number of Y)
-  R cr, ci;                  // effective coefficient coef * w_group * i^ipow
+  uint32_t lx, x, zm, zm2;
+  R cr, ci;    // effective coefficient coef * w_group * i^ipow
+  R cr2, ci2;  // the companion product's (0 if none)
 };
 
 // X-string product with a real coefficient: the hot case (driver and XX terms)
@@ -266,21 +267,28 @@ __device__ __forceinline__ void load_coefficients(TileCtx<R>& T, const DevTables
   }
   for (int k = threadIdx.x; k < T.ng; k += blockDim.x) {
     const DevFlip d = tab->flips[k < T.ngl ? fb + T.np + k : rb + (k - T.ngl)];
-    const double c = d.coef * pick3(w0, w1, w2, d.group);
-    double cr = 0.0, ci = 0.0;
-    switch (d.ipow & 3) {
-      case 0: cr = c; break;
-      case 1: ci = c; break;
-      case 2: cr = -c; break;
-      default: ci = -c; break;
-    }
+    // c * i^ipow as (re, im)
+    auto phased = [](double c, int ipow, double& cr, double& ci) {
+      cr = ci = 0.0;
+      switch (ipow & 3) {
+        case 0: cr = c; break;
+        case 1: ci = c; break;
+        case 2: cr = -c; break;
+        default: ci = -c; break;
+      }
+    };
+    double cr, ci, cr2 = 0.0, ci2 = 0.0;
+    phased(d.coef * pick3(w0, w1, w2, d.group), d.ipow, cr, ci);
+    if (d.has2) phased(d.coef2 * pick3(w0, w1, w2, d.group2), d.ipow2, cr2, ci2);
     SFlip<R> f;
     f.lx = k < T.ngl ? d.lx : 0u;
     f.x = d.x;
     f.zm = d.zm;
-    f.cplx = (d.ipow & 1);
+    f.zm2 = d.has2 ? d.zm2 : 0u;
     f.cr = (R)cr;
     f.ci = (R)ci;
+    f.cr2 = (R)cr2;
+    f.ci2 = (R)ci2;
     T.s_gf[k] = f;
   }
   for (int k = threadIdx.x; k < T.nz; k += blockDim.x) {
@@ -657,10 +665,20 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
       }
 #pragma unroll
       for (int g = 0; g < G; g++) {
+        const uint32_t zsrc = z[g] ^ f.x;
         R cr = f.cr, ci = f.ci;
-        if (__popc(f.zm & (z[g] ^ f.x)) & 1) {
+        if (__popc(f.zm & zsrc) & 1) {
           cr = -cr;
           ci = -ci;
+        }
+        // companion product of the same flip: its phase adds to the coefficient (exact
+        // cancellation where the two phases are opposite)
+        if (__popc(f.zm2 & zsrc) & 1) {
+          cr -= f.cr2;
+          ci -= f.ci2;
+        } else {
+          cr += f.cr2;
+          ci += f.ci2;
         }
         ar[g] += cr * u[g].x - ci * u[g].y;
         ai[g] += cr * u[g].y + ci * u[g].x;
@@ -1211,24 +1229,29 @@ cudaError_t launch_diag_codes(uint8_t* out, uint64_t N, const DevTables* tab, in
 }
 
 // ---- pointwise kernels ------------------------------------------------------------------
+// kind 0: uniform 1/sqrt(N) (|S>, Sec. II.A.1); 1: |basis>; 2: Dicke state of Hamming weight
+// `basis` (Eq. initstate), amplitude `amp` = C(n, basis)^(-1/2) on every index of that weight
 template <typename R>
-__global__ void k_init(typename Cplx<R>::T* y, uint64_t N, int kind, uint64_t basis) {
+__global__ void k_init(typename Cplx<R>::T* y, uint64_t N, int kind, uint64_t basis, double amp) {
   using C2 = typename Cplx<R>::T;
   const R u = (R)(1.0 / sqrt((double)N));
+  const R a = (R)amp;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
     if (kind == 0)
       y[i] = C2{u, (R)0};
-    else
+    else if (kind == 1)
       y[i] = C2{(R)(i == basis ? 1 : 0), (R)0};
+    else
+      y[i] = C2{(uint64_t)__popcll(i) == basis ? a : (R)0, (R)0};
   }
 }
 
-cudaError_t launch_init(int prec, void* y, uint64_t N, int kind, uint64_t basis, cudaStream_t s) {
+cudaError_t launch_init(int prec, void* y, uint64_t N, int kind, uint64_t basis, double amp, cudaStream_t s) {
   const int grid = (int)((N + 255) / 256 < 4096 ? (N + 255) / 256 : 4096);
   if (prec == 0)
-    k_init<double><<<grid, 256, 0, s>>>((double2*)y, N, kind, basis);
+    k_init<double><<<grid, 256, 0, s>>>((double2*)y, N, kind, basis, amp);
   else
-    k_init<float><<<grid, 256, 0, s>>>((float2*)y, N, kind, basis);
+    k_init<float><<<grid, 256, 0, s>>>((float2*)y, N, kind, basis, amp);
   return cudaGetLastError();
 }
 

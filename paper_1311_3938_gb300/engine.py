@@ -97,8 +97,11 @@ class Context:
         N.aqc_set_integrator(self.handle, n_steps, kappa)
 
     def set_initial_state(self, state="uniform"):
+        """"uniform" (|S>), a basis index, ("dicke", k) (Eq. initstate), or a host/device vector."""
         if isinstance(state, str) and state == "uniform":
             N.aqc_set_initial_state(self.handle, N.AQC_INIT_UNIFORM, 0, 0)
+        elif isinstance(state, tuple) and len(state) == 2 and state[0] == "dicke":
+            N.aqc_set_initial_state(self.handle, N.AQC_INIT_DICKE, int(state[1]), 0)
         elif isinstance(state, (int, np.integer)):
             N.aqc_set_initial_state(self.handle, N.AQC_INIT_BASIS, int(state), 0)
         elif isinstance(state, torch.Tensor) and state.device.type == "cpu":

@@ -62,6 +62,87 @@ def ec3_zz_terms(n: int, clauses, omega: float = 1.0):
     return np.array(xs, np.uint64), np.array(zs, np.uint64), np.array(cs, np.float64)
 
 
+def _pair_weights(clauses):
+    """n_ij (Eq. final_ham): clauses holding both bits i < j, as {(i, j): count}."""
+    out = {}
+    for c in clauses:
+        a, b, d = sorted(int(v) for v in c)
+        for key in ((a, b), (a, d), (b, d)):
+            out[key] = out.get(key, 0) + 1
+    return out
+
+
+def xyz_driver_terms(clauses, omega: float = 1.0):
+    """Eq. Hixyz: Omega sum_{i<j} n_ij/2 (1 - X_i X_j - Y_i Y_j - Z_i Z_j), the Heisenberg
+    ferromagnet on the clause graph.  A Y on qubit q sets bit q in both masks."""
+    xs, zs, cs = [], [], []
+    ident = 0.0
+    for (i, j), v in sorted(_pair_weights(clauses).items()):
+        m = (1 << i) | (1 << j)
+        a = omega * v / 2.0
+        ident += a
+        xs += [m, m, 0]
+        zs += [0, m, m]
+        cs += [-a, -a, -a]
+    return (np.array([0] + xs, np.uint64), np.array([0] + zs, np.uint64), np.array([ident] + cs, np.float64))
+
+
+def xy_driver_terms(clauses, omega: float = 1.0):
+    """Eq. Hixy: 3 m Omega 1 - Omega sum_{i<j} n_ij/2 (X_i X_j + Y_i Y_j), the x,y ferromagnet."""
+    xs, zs, cs = [0], [0], [3.0 * len(clauses) * omega]
+    for (i, j), v in sorted(_pair_weights(clauses).items()):
+        m = (1 << i) | (1 << j)
+        xs += [m, m]
+        zs += [0, m]
+        cs += [-omega * v / 2.0, -omega * v / 2.0]
+    return np.array(xs, np.uint64), np.array(zs, np.uint64), np.array(cs, np.float64)
+
+
+def removable_clauses(n: int, clauses):
+    """Indices of clauses whose removal keeps the clause graph connected (bits joined by shared
+    clauses), the clauses the paper allows to drop for H_{m-1} (Sec. IV.A.1)."""
+    used = sorted({int(b) for c in clauses for b in c})  # the bits of the full clause graph
+
+    def connected(cl):
+        parent = list(range(n))
+
+        def find(a):
+            while parent[a] != a:
+                parent[a] = parent[parent[a]]
+                a = parent[a]
+            return a
+
+        for c in cl:
+            r = find(int(c[0]))
+            for b in c[1:]:
+                parent[find(int(b))] = r
+        return len({find(b) for b in used}) <= 1
+
+    base = connected(clauses)
+    return [k for k in range(len(clauses)) if connected(clauses[:k] + clauses[k + 1:]) or not base]
+
+
+def load_xy(ctx, inst, driver: str = "xy", catalyst_alpha: float = 0.0, removed: int = None,
+            penalty=N.AQC_PEN_INDICATOR):
+    """The XY or XYZ algorithm (Sec. III.A.2-3) with optional catalyst (Eq. nlpath): driver in
+    group A, H_f clauses in group B and, if catalyst_alpha != 0, H_{m-1} (every clause but
+    `removed`; default: the last removable clause) in group C.  Returns the schedule (use
+    with ctx.set_schedule) and the Hamming weight of the solution (the Dicke start sector)."""
+    terms = xy_driver_terms(inst.clauses) if driver == "xy" else xyz_driver_terms(inst.clauses)
+    ctx.load_terms(N.AQC_GRP_A, *terms)
+    ctx.load_clauses(N.AQC_GRP_B, inst.clauses, penalty=penalty)
+    sched = linear_schedule()
+    if catalyst_alpha:
+        cl = list(inst.clauses)
+        if removed is None:
+            rem = removable_clauses(inst.n, cl)
+            removed = rem[-1] if rem else len(cl) - 1
+        keep = cl[:removed] + cl[removed + 1:]
+        ctx.load_clauses(N.AQC_GRP_C, keep, penalty=penalty)
+        sched = nonlinear_schedule(catalyst_alpha)
+    return sched, bin(int(inst.solution)).count("1")
+
+
 def clause_bits(clauses):
     """EC3 clauses (Eq. 1clause) as a flat int32 array of 0-based bits."""
     return np.ascontiguousarray(np.array(clauses, dtype=np.int32).reshape(-1))

@@ -37,6 +37,8 @@ class Job:
     precision: int = N.AQC_C64
     s_kind: int = N.AQC_S_LINEAR
     arrival: float = 0.0
+    driver: str = "x"      # "x" (Eq. Hix, start |S>), "xy" / "xyz" (Eq. Hixy / Hixyz, Dicke start)
+    alpha: float = 8.0     # catalyst strength of the XY/XYZ nonlinear path (Eq. nlpath)
     # filled in when the job is served
     admitted: float = math.nan
     finished: float = math.nan
@@ -77,10 +79,16 @@ def make_context(job: Job, device=0, stream=None, tile_bits=0) -> tuple:
     ctx = Context(job.n, job.precision, device=device, stream=stream)
     if tile_bits:
         ctx.set_tile_bits(tile_bits)
-    HB.load_ec3(ctx, inst, pairs=pairs)
-    ctx.set_schedule(job.T, HB.nonlinear_schedule() if job.nonlinear else HB.linear_schedule(), job.s_kind)
-    ctx.set_integrator(0, 0.0)
-    ctx.set_initial_state("uniform")
+    if job.driver == "x":
+        HB.load_ec3(ctx, inst, pairs=pairs)
+        ctx.set_schedule(job.T, HB.nonlinear_schedule() if job.nonlinear else HB.linear_schedule(), job.s_kind)
+        ctx.set_integrator(0, 0.0)
+        ctx.set_initial_state("uniform")
+    else:  # XY / XYZ algorithm; the nonlinear path adds the catalyst alpha s(1-s) H_{m-1}
+        sched, k = HB.load_xy(ctx, inst, driver=job.driver, catalyst_alpha=job.alpha if job.nonlinear else 0.0)
+        ctx.set_schedule(job.T, sched, job.s_kind)
+        ctx.set_integrator(0, 0.0)
+        ctx.set_initial_state(("dicke", k))
     return ctx, inst
 
 
@@ -229,15 +237,63 @@ def run_sequential(jobs, device=0, keep_state=False):
     return time.perf_counter() - t0
 
 
+def run_algorithms(n=13, seed=3, Ts=(2.0, 5.0, 10.0, 20.0, 50.0), precision=N.AQC_C64, device=0):
+    """The algorithms of Sec. III-IV on one instance: X (from |S>), XYZ and XY (from the Dicke
+    state of the solution's weight), and XY with the alpha = 8 catalyst (Eq. nlpath), each over
+    runtimes T: final P_1, energy E and wall seconds per solve."""
+    rows = []
+    for driver, nonlinear in (("x", False), ("xyz", False), ("xy", False), ("xy", True)):
+        for T in Ts:
+            job = Job(jid=0, n=n, seed=seed, nonlinear=nonlinear, T=T, precision=precision, driver=driver)
+            t0 = time.perf_counter()
+            solve_single(job, device)
+            rows.append({"algorithm": driver + ("+catalyst" if nonlinear else ""), "n": n, "T": T,
+                         "grid_steps": job.steps, "P1": job.P1, "E": job.E, "norm2_minus_1": job.norm2 - 1.0,
+                         "seconds": time.perf_counter() - t0})
+    return rows
+
+
+def run_ts_scaling(ns=(8, 10, 12, 14, 16), count=8, seed=5000, drivers=("x", "xy"), precision=N.AQC_C64,
+                   device=0):
+    """Median successful runtime T_s (E(T_s)/Omega = 1/2, Sec. III.B) over `count` seeded
+    instances per n and algorithm, each T_s found by batched solves (tsearch.find_Ts)."""
+    from .tsearch import find_Ts
+
+    rows = []
+    for n in ns:
+        for driver in drivers:
+            ts, evals = [], 0
+            t0 = time.perf_counter()
+            for k in range(count):
+                job = Job(jid=k, n=n, seed=seed + 100 * n + k, nonlinear=False, T=1.0, precision=precision,
+                          driver=driver)
+                r = find_Ts(job, T_lo=1.0, T_hi=64.0, k=8, rtol=1e-2, device=device)
+                evals += r["evaluations"]
+                if r["Ts"] is not None:
+                    ts.append(r["Ts"])
+            rows.append({"n": n, "algorithm": driver, "instances": count, "found": len(ts),
+                         "median_Ts": float(np.median(ts)) if ts else None,
+                         "min_Ts": min(ts) if ts else None, "max_Ts": max(ts) if ts else None,
+                         "solves": evals, "seconds": time.perf_counter() - t0})
+    return rows
+
+
 def _main():
     import argparse
     import json
 
     ap = argparse.ArgumentParser(description="workload drivers")
-    ap.add_argument("what", choices=["sweep20"])
+    ap.add_argument("what", choices=["sweep20", "algorithms", "ts"])
+    ap.add_argument("--n", type=int, default=13)
     a = ap.parse_args()
     if a.what == "sweep20":
         for row in run_sweep_n20():
+            print(json.dumps(row), flush=True)
+    elif a.what == "algorithms":
+        for row in run_algorithms(n=a.n):
+            print(json.dumps(row), flush=True)
+    elif a.what == "ts":
+        for row in run_ts_scaling():
             print(json.dumps(row), flush=True)
 
 

@@ -1,0 +1,69 @@
+"""T_s search (Sec. III.B) logic on the CPU: closed-form energy curves and oracle solves."""
+import math
+
+import pytest
+
+from instances import generate_ec3
+from oracle import oracle as O
+
+
+def test_exponential_energy_curve():
+    from paper_1311_3938_gb300.tsearch import search_Ts
+
+    calls = []
+
+    def E(Ts):
+        calls.append(len(Ts))
+        return [math.exp(-T / 10.0) for T in Ts]
+
+    r = search_Ts(E, 1.0, 64.0, k=8, rtol=1e-4)
+    assert abs(r["Ts"] - 10.0 * math.log(2.0)) < 1e-3
+    assert all(c <= 8 for c in calls)
+
+
+@pytest.mark.parametrize("lo,hi", [(0.01, 0.05), (500.0, 900.0)])
+def test_bracket_is_widened(lo, hi):
+    from paper_1311_3938_gb300.tsearch import search_Ts
+
+    r = search_Ts(lambda Ts: [1.0 / (1.0 + T / 7.0) for T in Ts], lo, hi, rtol=1e-5)
+    assert abs(r["Ts"] - 7.0) < 1e-3
+
+
+def test_first_crossing_of_a_non_monotone_curve():
+    """E dips below 1/2 near T = 5, comes back above, and falls for good later: the first
+    crossing is the one reported, with E above target just before it on the search grids."""
+    from paper_1311_3938_gb300.tsearch import search_Ts
+
+    def e(T):
+        return 0.9 * math.exp(-T / 8.0) + 0.25 * math.sin(T) ** 2 * math.exp(-T / 30.0)
+
+    r = search_Ts(lambda Ts: [e(T) for T in Ts], 0.5, 60.0, k=16, rtol=1e-6)
+    assert abs(e(r["Ts"]) - 0.5) < 1e-4
+    # a brute-force scan finds no earlier crossing than the reported bracket's lower end
+    lo = r["bracket"][0]
+    T = 0.5
+    while T < lo:
+        assert e(T) > 0.5 or T > lo * 0.999
+        T *= 1.0005
+
+
+def test_oracle_solves_x_algorithm():
+    """n = 6 EC3 instance, X algorithm: the T_s found from oracle solves has E(T_s) = 1/2 up to
+    the bracket resolution, and the energy is above 1/2 at the bracket's lower end."""
+    from paper_1311_3938_gb300.tsearch import search_Ts
+
+    inst = generate_ec3(6, 2)
+    H = O.ec3_hamiltonian(inst)
+
+    def E(Ts):
+        out = []
+        for T in Ts:
+            sched = O.linear_path(T)
+            res = O.propagate(H, sched, O.step_count(H, sched), O.uniform_state(6))
+            out.append(O.energy(H, res.psi, 1))
+        return out
+
+    r = search_Ts(E, 1.0, 64.0, k=6, rtol=1e-3)
+    assert r["Ts"] is not None
+    assert abs(E([r["Ts"]])[0] - 0.5) < 5e-3
+    assert E([r["bracket"][0]])[0] > 0.5
