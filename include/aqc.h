@@ -231,6 +231,32 @@ int aqc_batch_poll(aqc_batch *b, int64_t *steps_done, int *active_out, int64_t *
 /* Message of the last error of b (or of the last failed aqc_batch_create if b is NULL). */
 const char *aqc_batch_last_error(const aqc_batch *b);
 
+/* ---- spectrum along the path (Sec. IV.B: gap above the ground state) ------------------ */
+
+/* Bytes of the caller-owned device memory aqc_lanczos needs for max_iter iterations: the
+ * Krylov basis (max_iter + 1 state vectors) plus reduction scratch; 0 for bad arguments. */
+size_t aqc_lanczos_workspace_bytes(int n_qubits, int precision, int max_iter);
+
+/* Lowest eigenvalues of H(t) by the Lanczos method with full reorthogonalisation (classical
+ * Gram-Schmidt twice per step, FP64 inner products) on the SQH matvec of aqc_hpsi.  The Krylov
+ * space starts from the caller's device vector `start` (2^n amplitudes, state precision, need
+ * not be normalised): for a Hamiltonian that conserves the Hamming weight (Eq. Sigmaz), a start
+ * inside one sector (AQC_INIT_DICKE state) gives that sector's spectrum.  Each distinct
+ * eigenvalue reachable from `start` appears once.  `work` (device, work_bytes >=
+ * aqc_lanczos_workspace_bytes) is scratch.  Stops after max_iter steps, on an invariant
+ * subspace, or when the n_eig lowest Ritz values moved by at most tol * max(1, |value|) over the
+ * last 8 steps.  Writes the n_eig lowest Ritz values in ascending order to eig[] and their last
+ * change to conv[] (host arrays of n_eig doubles; conv may be NULL) and the steps taken to
+ * *iters_out (may be NULL).  Uses the context's partial-sum vector (not during a propagation
+ * call); synchronises the context stream. */
+int aqc_lanczos(aqc_ctx *ctx, double t, const void *start, void *work, size_t work_bytes, int max_iter, int n_eig,
+                double tol, double *eig, double *conv, int *iters_out);
+
+/* Host helper (no device work): the n_eig lowest eigenvalues, ascending, of the symmetric
+ * tridiagonal matrix with diagonal a[0..k) and off-diagonal b[0..k-1), by Sturm-sequence
+ * bisection to full double precision. */
+int aqc_tridiag_eigvals(int k, const double *a, const double *b, int n_eig, double *out);
+
 /* ---- entry point that allocates nothing ---------------------------------------------- */
 
 /* Bytes of the library's static device scratch used by aqc_norm2_noalloc (per device). */

@@ -84,6 +84,10 @@ def lib():
             "aqc_energy": (i32, [vp, i32, C.POINTER(dbl)]),
             "aqc_norm2": (i32, [vp, C.POINTER(dbl)]),
             "aqc_hpsi": (i32, [vp, dbl, vp, vp]),
+            "aqc_lanczos_workspace_bytes": (sz, [i32, i32, i32]),
+            "aqc_lanczos": (i32, [vp, dbl, vp, vp, sz, i32, i32, dbl, C.POINTER(dbl), C.POINTER(dbl),
+                                  C.POINTER(i32)]),
+            "aqc_tridiag_eigvals": (i32, [i32, C.POINTER(dbl), C.POINTER(dbl), i32, C.POINTER(dbl)]),
             "aqc_launch_count": (i32, [vp, C.POINTER(i64)]),
             "aqc_batch_workspace_bytes": (sz, [i32, i64]),
             "aqc_batch_create": (i32, [C.POINTER(vp), i32, i32, i32, i64, vp, sz, vp]),
@@ -211,6 +215,31 @@ def aqc_norm2(ctx):
 
 def aqc_hpsi(ctx, t, psi_ptr, out_ptr):
     _check(ctx, lib().aqc_hpsi(ctx, float(t), C.c_void_p(psi_ptr), C.c_void_p(out_ptr)))
+
+
+def aqc_lanczos_workspace_bytes(n, precision, max_iter):
+    return int(lib().aqc_lanczos_workspace_bytes(int(n), int(precision), int(max_iter)))
+
+
+def aqc_lanczos(ctx, t, start_ptr, work_ptr, work_bytes, max_iter, n_eig, tol):
+    """(eigenvalues, their last change, iterations) of the lowest n_eig Ritz values."""
+    eig = (C.c_double * n_eig)()
+    conv = (C.c_double * n_eig)()
+    iters = C.c_int()
+    _check(ctx, lib().aqc_lanczos(ctx, float(t), C.c_void_p(start_ptr), C.c_void_p(work_ptr), int(work_bytes),
+                                  int(max_iter), int(n_eig), float(tol), eig, conv, C.byref(iters)))
+    return list(eig), list(conv), iters.value
+
+
+def aqc_tridiag_eigvals(a, b, n_eig):
+    k = len(a)
+    A = (C.c_double * k)(*a)
+    B = (C.c_double * max(1, k - 1))(*b) if k > 1 else (C.c_double * 1)()
+    out = (C.c_double * n_eig)()
+    rc = lib().aqc_tridiag_eigvals(k, A, B, int(n_eig), out)
+    if rc:
+        raise AqcError(rc, "aqc_tridiag_eigvals: bad arguments")
+    return list(out)
 
 
 def aqc_launch_count(ctx):

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libaqc.so")
-SOURCES = ["api.cu", "kernels.cu", "xpartial.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "kernels.cu", "xpartial.cu", "lanczos.cu", "noalloc.cu"]
 HEADERS = ["aqc_internal.h", os.path.join("..", "..", "include", "aqc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -1143,6 +1143,62 @@ int aqc_norm2(aqc_ctx* ctx, double* out) {
   return read_slot(ctx, kSlotNorm2, out);
 }
 
+// ---- Lanczos (spectrum along the path) ----------------------------------------------------
+namespace {
+
+// eigenvalues of the symmetric tridiagonal (a, b) below x (Sturm sequence of the LDL^T pivots)
+int sturm_below(const double* a, const double* b, int k, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < k; i++) {
+    d = (a[i] - x) - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) cnt++;
+  }
+  return cnt;
+}
+
+// j-th smallest eigenvalue (0-based) by bisection inside the Gershgorin interval
+double tridiag_eig(const double* a, const double* b, int k, int j) {
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < k; i++) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < k - 1 ? fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200; it++) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;  // interval at the resolution of doubles
+    if (sturm_below(a, b, k, mid) > j)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+struct LzPlan {
+  size_t ld_bytes, off_partials, off_coef, off_h, off_scal, total;
+  uint32_t G;
+};
+
+LzPlan lanczos_plan(int n, int prec, int max_iter) {
+  LzPlan p;
+  const uint64_t N = (uint64_t)1 << n;
+  const size_t amp = prec == AQC_C128 ? 16 : 8;
+  p.ld_bytes = align_up(N * amp, 256);
+  const size_t m = (size_t)max_iter + 1;
+  p.G = lanczos_dot_blocks(N);
+  p.off_partials = m * p.ld_bytes;
+  p.off_coef = align_up(p.off_partials + m * p.G * 2 * sizeof(double), 256);
+  p.off_h = align_up(p.off_coef + m * 2 * sizeof(double), 256);
+  p.off_scal = align_up(p.off_h + m * 2 * sizeof(double), 256);
+  p.total = p.off_scal + 256;
+  return p;
+}
+
+}  // namespace
+
 int aqc_hpsi(aqc_ctx* ctx, double t, const void* psi, void* out) {
   if (!ctx) return AQC_E_INVAL;
   if (!psi || !out || psi == out) FAIL(ctx, AQC_E_INVAL, "psi and out must be distinct device pointers");
@@ -1365,5 +1421,105 @@ const char* aqc_last_error(const aqc_ctx* ctx) {
 }
 
 const char* aqc_version(void) { return "aqc-gb300 0.1.0 (sm_103a)"; }
+
+
+
+size_t aqc_lanczos_workspace_bytes(int n_qubits, int precision, int max_iter) {
+  if (n_qubits < 1 || n_qubits > kMaxN || (precision != AQC_C128 && precision != AQC_C64) || max_iter < 1 ||
+      max_iter > 4096)
+    return 0;
+  return lanczos_plan(n_qubits, precision, max_iter).total;
+}
+
+int aqc_tridiag_eigvals(int k, const double* a, const double* b, int n_eig, double* out) {
+  if (k < 1 || !a || (k > 1 && !b) || n_eig < 1 || n_eig > k || !out) return AQC_E_INVAL;
+  for (int j = 0; j < n_eig; j++) out[j] = tridiag_eig(a, b, k, j);
+  return AQC_OK;
+}
+
+int aqc_lanczos(aqc_ctx* ctx, double t, const void* start, void* work, size_t work_bytes, int max_iter, int n_eig,
+                double tol, double* eig, double* conv, int* iters_out) {
+  if (!ctx) return AQC_E_INVAL;
+  if (!start || !work || !eig) FAIL(ctx, AQC_E_INVAL, "start, work and eig must be non-NULL");
+  if (max_iter < 1 || max_iter > 4096 || n_eig < 1 || n_eig > max_iter || !(tol >= 0.0))
+    FAIL(ctx, AQC_E_INVAL, "need 1 <= n_eig <= max_iter <= 4096 and tol >= 0");
+  const LzPlan P = lanczos_plan(ctx->n, ctx->prec, max_iter);
+  if (work_bytes < P.total) FAIL(ctx, AQC_E_NOMEM, "work has %zu bytes, %zu needed", work_bytes, P.total);
+  if (((uintptr_t)work & 255u) || ((uintptr_t)start & 15u)) FAIL(ctx, AQC_E_INVAL, "work must be 256-byte aligned");
+  if (!ctx->have_sched) FAIL(ctx, AQC_E_STATE, "no schedule set");
+  DeviceGuard dg(ctx->device);
+  if (ctx->dirty) {
+    int rc = build_tables(ctx);
+    if (rc) return rc;
+  }
+  double w[3];
+  sched_weights(ctx, t, w);
+  char* base = (char*)work;
+  const uint64_t ld = P.ld_bytes / ctx->amp;  // elements between basis vectors
+  auto V = [&](int i) { return (void*)(base + (size_t)i * P.ld_bytes); };
+  double* partials = (double*)(base + P.off_partials);
+  double* coef = (double*)(base + P.off_coef);
+  double* h = (double*)(base + P.off_h);
+  double* scal = (double*)(base + P.off_scal);
+  cudaStream_t s = ctx->stream;
+  const uint64_t N = ctx->N;
+  // v_0 = start / ||start||
+  CUDA_TRY(ctx, cudaMemcpyAsync(V(0), start, N * ctx->amp, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(ctx, launch_dotc_multi(ctx->prec, V(0), ld, 1, V(0), N, partials, scal, nullptr, s));
+  CUDA_TRY(ctx, launch_scale_to(ctx->prec, V(0), V(0), N, scal, s));
+  ctx->launches += 3;
+  std::vector<double> alpha, beta, prev(n_eig, 0.0), cur(n_eig, 0.0), chg(n_eig, INFINITY);
+  int iters = 0;
+  bool have_prev = false;
+  for (int j = 0; j < max_iter; j++) {
+    void* wv = V(j + 1);
+    ApplyParams fin = base_params(ctx);
+    fin.mode = MODE_PARTIAL;
+    int rc = evaluate(ctx, w, V(j), fin, wv);
+    if (rc) return rc;
+    CUDA_TRY(ctx, cudaMemsetAsync(h, 0, (size_t)(j + 1) * 2 * sizeof(double), s));
+    for (int pass = 0; pass < 2; pass++) {  // classical Gram-Schmidt, twice
+      CUDA_TRY(ctx, launch_dotc_multi(ctx->prec, V(0), ld, (uint32_t)(j + 1), wv, N, partials, coef, h, s));
+      CUDA_TRY(ctx, launch_sub_multi(ctx->prec, wv, V(0), ld, (uint32_t)(j + 1), coef, N, s));
+      ctx->launches += 3;
+    }
+    CUDA_TRY(ctx, launch_dotc_multi(ctx->prec, wv, ld, 1, wv, N, partials, scal, nullptr, s));
+    ctx->launches += 2;
+    double hj[2], nrm2[2];
+    CUDA_TRY(ctx, cudaMemcpyAsync(hj, h + 2 * j, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaMemcpyAsync(nrm2, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (!std::isfinite(hj[0]) || !std::isfinite(nrm2[0])) FAIL(ctx, AQC_E_NUMERIC, "non-finite Lanczos coefficient");
+    alpha.push_back(hj[0]);
+    const double bj = sqrt(std::max(nrm2[0], 0.0));
+    iters = j + 1;
+    const bool invariant = bj <= 1e-13 * std::max(1.0, fabs(hj[0]));
+    const int m = std::min(n_eig, iters);
+    const bool check = invariant || iters == max_iter || iters % 8 == 0;
+    if (check && iters >= n_eig) {
+      for (int e = 0; e < m; e++) cur[e] = tridiag_eig(alpha.data(), beta.data(), iters, e);
+      bool done = have_prev;
+      for (int e = 0; e < m; e++) {
+        chg[e] = have_prev ? fabs(cur[e] - prev[e]) : INFINITY;
+        done = done && chg[e] <= tol * std::max(1.0, fabs(cur[e]));
+      }
+      prev = cur;
+      have_prev = true;
+      if (done || invariant) break;
+    }
+    if (invariant) break;
+    beta.push_back(bj);
+    CUDA_TRY(ctx, launch_scale_to(ctx->prec, wv, wv, N, scal, s));
+    ctx->launches++;
+  }
+  CUDA_TRY(ctx, cudaStreamSynchronize(s));  // the caller's work buffer is free on return
+  const int m = std::min(n_eig, iters);
+  for (int e = 0; e < n_eig; e++) {
+    eig[e] = e < m ? tridiag_eig(alpha.data(), beta.data(), iters, e) : NAN;
+    if (conv) conv[e] = e < m ? chg[e] : NAN;
+  }
+  if (iters_out) *iters_out = iters;
+  return AQC_OK;
+}
 
 }  // extern "C"

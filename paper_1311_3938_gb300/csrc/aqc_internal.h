@@ -224,6 +224,12 @@ cudaError_t launch_slab(int prec, const SlabParams& p, int smem_bytes, cudaStrea
 bool xpartial_layout_ok(const Layout& L);
 size_t xpartial_smem_bytes(int n_flips);
 cudaError_t launch_partial_x(const XPartialParams& p, int smem_bytes, cudaStream_t s);
+uint32_t lanczos_dot_blocks(uint64_t N);
+cudaError_t launch_dotc_multi(int prec, const void* V, uint64_t ld, uint32_t m, const void* w, uint64_t N,
+                              double* partials, double* out, double* acc, cudaStream_t s);
+cudaError_t launch_sub_multi(int prec, void* w, const void* V, uint64_t ld, uint32_t m, const double* c, uint64_t N,
+                             cudaStream_t s);
+cudaError_t launch_scale_to(int prec, void* v, const void* w, uint64_t N, const double* nrm2, cudaStream_t s);
 cudaError_t launch_diag_codes(uint8_t* out, uint64_t N, const DevTables* tab, int cls, cudaStream_t s);
 cudaError_t launch_init(int prec, void* y, uint64_t N, int kind, uint64_t basis, double amp, cudaStream_t s);
 cudaError_t launch_predict(int prec, void* p, const void* y, const void* f3, const void* f2, const void* f1,

@@ -153,6 +153,18 @@ class Context:
     def launch_count(self):
         return N.aqc_launch_count(self.handle)
 
+    def lanczos(self, t, start: torch.Tensor, max_iter=200, n_eig=2, tol=1e-10):
+        """Lowest n_eig eigenvalues of H(t) reachable from `start` (aqc_lanczos): returns
+        (eigenvalues, last change of each, iterations)."""
+        nbytes = N.aqc_lanczos_workspace_bytes(self.n, self.precision, max_iter)
+        with torch.cuda.stream(self.stream):
+            start = start.to(self.dev, _torch_dtype(self.precision)).contiguous()
+            work = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.dev)
+            off = (-work.data_ptr()) % 256
+            out = N.aqc_lanczos(self.handle, t, start.data_ptr(), work.data_ptr() + off, nbytes, max_iter, n_eig, tol)
+            del work, start
+        return out
+
     def hpsi(self, t, psi: torch.Tensor, out: torch.Tensor = None):
         """out = H(t) psi for device tensors of the state dtype."""
         psi = psi.to(self.dev, _torch_dtype(self.precision)).contiguous()

@@ -278,12 +278,48 @@ def run_ts_scaling(ns=(8, 10, 12, 14, 16), count=8, seed=5000, drivers=("x", "xy
     return rows
 
 
+def run_gap_curves(n=13, seed=3, s_points=25, precision=N.AQC_C128, device=0, max_iter=200):
+    """Gap between the two lowest eigenvalues of H(s) along the path (Fig. 41N13, bottom) for
+    the X algorithm (full space, random start), the XY algorithm and the XY algorithm with the
+    alpha = 8 catalyst (solution's Hamming-weight sector, Dicke start), by aqc_lanczos; minimum
+    gap, where it sits, and milliseconds per Lanczos solve."""
+    from instances import random_state
+
+    inst = _instance(n, seed)
+    k = bin(int(inst.solution)).count("1")
+    s_grid = [0.02 + 0.96 * i / (s_points - 1) for i in range(s_points)]
+    rows = []
+    for driver, alpha in (("x", 0.0), ("xy", 0.0), ("xy", 8.0)):
+        ctx = Context(n, precision, device=device)
+        if driver == "x":
+            HB.load_ec3(ctx, inst)
+            ctx.set_schedule(1.0, HB.linear_schedule())
+            start = torch.from_numpy(random_state(n, seed)).to(ctx.dev)
+        else:
+            sched, _ = HB.load_xy(ctx, inst, driver=driver, catalyst_alpha=alpha)
+            ctx.set_schedule(1.0, sched)
+            ctx.set_initial_state(("dicke", k))
+            start = ctx.state(device=True)
+        gaps, ms = [], []
+        for sv in s_grid:
+            t0 = time.perf_counter()
+            eig, conv, iters = ctx.lanczos(sv, start, max_iter=max_iter, n_eig=2, tol=1e-11)
+            ms.append((time.perf_counter() - t0) * 1e3)
+            gaps.append(eig[1] - eig[0])
+        ctx.close()
+        j = int(np.argmin(gaps))
+        rows.append({"algorithm": driver + ("+catalyst" if alpha else ""), "n": n, "sector_weight": None if driver == "x" else k,
+                     "min_gap": gaps[j], "s_at_min": s_grid[j], "gaps": gaps, "s": s_grid,
+                     "ms_per_lanczos": float(np.median(ms))})
+    return rows
+
+
 def _main():
     import argparse
     import json
 
     ap = argparse.ArgumentParser(description="workload drivers")
-    ap.add_argument("what", choices=["sweep20", "algorithms", "ts"])
+    ap.add_argument("what", choices=["sweep20", "algorithms", "ts", "gap"])
     ap.add_argument("--n", type=int, default=13)
     a = ap.parse_args()
     if a.what == "sweep20":
@@ -294,6 +330,9 @@ def _main():
             print(json.dumps(row), flush=True)
     elif a.what == "ts":
         for row in run_ts_scaling():
+            print(json.dumps(row), flush=True)
+    elif a.what == "gap":
+        for row in run_gap_curves(n=a.n):
             print(json.dumps(row), flush=True)
 
 
