@@ -17,10 +17,11 @@ def _geom(lo, hi, k):
     return [lo * (hi / lo) ** (i / (k - 1)) for i in range(k)]
 
 
-def search_Ts(energies, T_lo, T_hi, target=0.5, k=8, rtol=1e-3, max_rounds=16, max_expand=8):
+def search_Ts(energies, T_lo, T_hi, target=0.5, k=8, rtol=1e-3, max_rounds=16, max_expand=8, T_max=1024.0):
     """First crossing of E(T) = target between T_lo and T_hi (widened by factors of 4 if E at
-    the ends does not straddle the target).  energies(list of T) -> list of E.  Returns a dict:
-    Ts (None if no crossing was found), bracket, rounds, evaluations."""
+    the ends does not straddle the target, never beyond T_max: a path whose gap closes never
+    reaches the target).  energies(list of T) -> list of E.  Returns a dict: Ts (None if no
+    crossing was found), bracket, rounds, evaluations."""
     if not (0 < T_lo < T_hi) or k < 3:
         raise ValueError("need 0 < T_lo < T_hi and k >= 3")
     seen = {}
@@ -37,8 +38,10 @@ def search_Ts(energies, T_lo, T_hi, target=0.5, k=8, rtol=1e-3, max_rounds=16, m
         e_lo, e_hi = ev([lo, hi])
         if e_lo <= target:  # already adiabatic enough at lo: the crossing lies below
             lo, hi = lo / 4.0, lo
-        elif e_hi > target:  # not yet at hi: look further up
-            lo, hi = hi, hi * 4.0
+        elif e_hi > target:  # not yet at hi: look further up, up to T_max
+            if hi >= T_max:
+                return {"Ts": None, "bracket": (lo, hi), "rounds": 0, "evaluations": len(seen)}
+            lo, hi = hi, min(hi * 4.0, T_max)
         else:
             break
     else:
@@ -73,6 +76,6 @@ def gpu_energies(job, device=0, batch_max_n=22):
     return f
 
 
-def find_Ts(job, T_lo=1.0, T_hi=64.0, k=8, rtol=1e-2, device=0):
+def find_Ts(job, T_lo=1.0, T_hi=64.0, k=8, rtol=1e-2, device=0, T_max=1024.0):
     """T_s of one job template (its T is ignored)."""
-    return search_Ts(gpu_energies(job, device), T_lo, T_hi, k=k, rtol=rtol)
+    return search_Ts(gpu_energies(job, device), T_lo, T_hi, k=k, rtol=rtol, T_max=T_max)

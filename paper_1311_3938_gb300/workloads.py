@@ -253,8 +253,8 @@ def run_algorithms(n=13, seed=3, Ts=(2.0, 5.0, 10.0, 20.0, 50.0), precision=N.AQ
     return rows
 
 
-def run_ts_scaling(ns=(8, 10, 12, 14, 16), count=8, seed=5000, drivers=("x", "xy"), precision=N.AQC_C64,
-                   device=0):
+def run_ts_scaling(ns=(6, 8, 10, 12), count=8, seed=5000, drivers=("x", "xy"), precision=N.AQC_C64,
+                   device=0, T_max=512.0):
     """Median successful runtime T_s (E(T_s)/Omega = 1/2, Sec. III.B) over `count` seeded
     instances per n and algorithm, each T_s found by batched solves (tsearch.find_Ts)."""
     from .tsearch import find_Ts
@@ -267,7 +267,7 @@ def run_ts_scaling(ns=(8, 10, 12, 14, 16), count=8, seed=5000, drivers=("x", "xy
             for k in range(count):
                 job = Job(jid=k, n=n, seed=seed + 100 * n + k, nonlinear=False, T=1.0, precision=precision,
                           driver=driver)
-                r = find_Ts(job, T_lo=1.0, T_hi=64.0, k=8, rtol=1e-2, device=device)
+                r = find_Ts(job, T_lo=1.0, T_hi=64.0, k=8, rtol=1e-2, device=device, T_max=T_max)
                 evals += r["evaluations"]
                 if r["Ts"] is not None:
                     ts.append(r["Ts"])

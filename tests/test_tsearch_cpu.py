@@ -67,3 +67,16 @@ def test_oracle_solves_x_algorithm():
     assert r["Ts"] is not None
     assert abs(E([r["Ts"]])[0] - 0.5) < 5e-3
     assert E([r["bracket"][0]])[0] > 0.5
+
+
+def test_no_crossing_below_T_max():
+    from paper_1311_3938_gb300.tsearch import search_Ts
+
+    seen = []
+
+    def E(Ts):
+        seen.extend(Ts)
+        return [0.6 + 0.4 / (1.0 + T) for T in Ts]  # never reaches 1/2
+
+    r = search_Ts(E, 1.0, 64.0, T_max=300.0)
+    assert r["Ts"] is None and max(seen) <= 300.0
