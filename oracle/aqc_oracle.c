@@ -12,7 +12,9 @@
  *     sign, sigma^y = both with a factor i) and the result is scattered into the output.
  *     Clause penalties of Exact Cover 3 (Eq. hci, Eq. sat) are diagonal in |z>.
  *   - Time-dependent coefficients (Sec. I.A last paragraph; Eq. aqc, Eq. nlpath):
- *     H(t) = sum_g w_g(s(t)) H_g with w_g a cubic polynomial in s.
+ *     H(t) = sum_g w_g(s(t)) H_g with w_g a cubic polynomial in s; clauses marked as a
+ *     clause-by-clause sequence (Eq. cbc, Eq. kpath) get in addition their coefficient in
+ *     H_d(s), evaluated from the definition term by term.
  *   - Integration of i d/dt psi = H(t) psi (Eq. schroedinger, hbar = 1) with a fourth-order
  *     predictor-corrector that evaluates H|psi> once per step (Sec. I.B): Adams-Bashforth-4
  *     predictor, Adams-Moulton-4 corrector, PEC mode, fixed step h = T/N, started with three
@@ -39,6 +41,8 @@ typedef struct {
   const int *clause_group;
   const int *clause_penalty;   /* 0: [k != 1] (indicator), 1: (1-k)^2 (Eq. hci)            */
   const double *clause_scale;  /* Omega                                                    */
+  const int *clause_step;      /* 0, or j >= 1: clause h_j of the clause-by-clause sequence */
+  int step_m;                  /* m: length of that sequence (Eq. kpath)                    */
 } or_ham;
 
 /* ---- schedule: s(t) and the three group weights ------------------------------------ */
@@ -48,10 +52,12 @@ typedef struct {
   double poly[3][4]; /* w_g(s) = sum_k poly[g][k] s^k */
 } or_sched;
 
-void or_weights(const or_sched *sc, double t, double w[3]) {
+/* w[0..2]: group weights at t; w[3]: the path parameter s(t) */
+void or_weights(const or_sched *sc, double t, double w[4]) {
   double tau = t / sc->T;
   double s = tau;
   if (sc->s_kind == 1) s = 3.0 * tau * tau - 2.0 * tau * tau * tau;
+  w[3] = s;
   for (int g = 0; g < 3; g++) {
     double v = 0.0, sk = 1.0;
     for (int k = 0; k < 4; k++) {
@@ -94,6 +100,29 @@ static double clause_penalty(int kind, int k) {
   return k == 1 ? 0.0 : 1.0;
 }
 
+/* Coefficient of clause h_j (1-based) in Eq. kpath:
+ *   H_d(s) = sum_{k=1}^{m} [(1 - s_k) H_{k-1} + s_k H_k] Theta(s_k) Theta(1 - s_k),
+ *   s_k = m s - k + 1,  H_k = h_1 + ... + h_k (1 <= k <= m-1),  H_0 = H_m = 0.
+ * Theta(s_k) Theta(1 - s_k) is read as s_k in [0, 1), so every s lies in one segment. */
+static double kpath_coef(int j, int m, double s) {
+  double c = 0.0;
+  for (int k = 1; k <= m; k++) {
+    double sk = (double)m * s - (double)k + 1.0;
+    if (!(sk >= 0.0 && sk < 1.0)) continue;
+    int in_prev = (k - 1 >= 1) && (k - 1 <= m - 1) && (j <= k - 1); /* h_j is part of H_{k-1} */
+    int in_cur = (k <= m - 1) && (j <= k);                           /* h_j is part of H_k */
+    c += (1.0 - sk) * (double)in_prev + sk * (double)in_cur;
+  }
+  return c;
+}
+
+/* weight of clause k of H at the weights w (w[3] = s) */
+static double clause_weight(const or_ham *H, const double *w, int k) {
+  double g = w[H->clause_group[k]] * H->clause_scale[k];
+  if (H->clause_step && H->clause_step[k] > 0) g *= kpath_coef(H->clause_step[k], H->step_m, w[3]);
+  return g;
+}
+
 static void *scatter_worker(void *arg) {
   or_job *jb = (or_job *)arg;
   const or_ham *H = jb->H;
@@ -124,7 +153,7 @@ static void *scatter_worker(void *arg) {
     for (int k = 0; k < H->nclauses; k++) {
       const int *cb = H->clause_bits + 3 * k;
       int ones = (int)((z >> cb[0]) & 1u) + (int)((z >> cb[1]) & 1u) + (int)((z >> cb[2]) & 1u);
-      d += jb->w[H->clause_group[k]] * H->clause_scale[k] * clause_penalty(H->clause_penalty[k], ones);
+      d += clause_weight(H, jb->w, k) * clause_penalty(H->clause_penalty[k], ones);
     }
     jb->out[2 * z] += d * jb->psi[2 * z];
     jb->out[2 * z + 1] += d * jb->psi[2 * z + 1];
@@ -133,7 +162,7 @@ static void *scatter_worker(void *arg) {
 }
 
 /* out = sum_g w_g H_g psi; psi and out are interleaved (re, im), length 2*2^n */
-int or_hpsi(const or_ham *H, const double w[3], const double *psi, double *out, int nthreads) {
+int or_hpsi(const or_ham *H, const double w[4], const double *psi, double *out, int nthreads) {
   uint64_t N = 1ull << H->n;
   memset(out, 0, sizeof(double) * 2 * N);
   if (nthreads < 1) nthreads = 1;
@@ -171,7 +200,7 @@ int or_hpsi(const or_ham *H, const double w[3], const double *psi, double *out, 
  * matrix element <z|P|z'>) * psi[z'], the element being built qubit by qubit as in the scatter
  * loop; clause penalties add their diagonal value at z.  Used to check single outputs of very
  * large states. */
-int or_hpsi_at(const or_ham *H, const double w[3], const double *psi, int64_t nz, const uint64_t *zs, double *out) {
+int or_hpsi_at(const or_ham *H, const double w[4], const double *psi, int64_t nz, const uint64_t *zs, double *out) {
   for (int64_t k = 0; k < nz; k++) {
     const uint64_t z = zs[k];
     double acc_re = 0.0, acc_im = 0.0;
@@ -197,7 +226,7 @@ int or_hpsi_at(const or_ham *H, const double w[3], const double *psi, int64_t nz
     for (int j = 0; j < H->nclauses; j++) {
       const int *cb = H->clause_bits + 3 * j;
       int ones = (int)((z >> cb[0]) & 1u) + (int)((z >> cb[1]) & 1u) + (int)((z >> cb[2]) & 1u);
-      d += w[H->clause_group[j]] * H->clause_scale[j] * clause_penalty(H->clause_penalty[j], ones);
+      d += clause_weight(H, w, j) * clause_penalty(H->clause_penalty[j], ones);
     }
     out[2 * k] = acc_re + d * psi[2 * z];
     out[2 * k + 1] = acc_im + d * psi[2 * z + 1];
@@ -208,7 +237,7 @@ int or_hpsi_at(const or_ham *H, const double w[3], const double *psi, int64_t nz
 /* f = -i H(t) y   (Eq. schroedinger with hbar = 1) */
 static int deriv(const or_ham *H, const or_sched *sc, double t, const double *y, double *f, double *tmp,
                  uint64_t N, int nthreads) {
-  double w[3];
+  double w[4];
   or_weights(sc, t, w);
   if (or_hpsi(H, w, y, tmp, nthreads) != 0) return -1;
   for (uint64_t z = 0; z < N; z++) {

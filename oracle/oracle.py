@@ -65,6 +65,8 @@ class _Ham(C.Structure):
         ("clause_group", C.POINTER(C.c_int)),
         ("clause_penalty", C.POINTER(C.c_int)),
         ("clause_scale", C.POINTER(C.c_double)),
+        ("clause_step", C.POINTER(C.c_int)),
+        ("step_m", C.c_int),
     ]
 
 
@@ -107,13 +109,14 @@ def _load():
 class Hamiltonian:
     n: int
     terms: list = field(default_factory=list)    # (group, xmask, zmask, coef)
-    clauses: list = field(default_factory=list)  # (group, (a, b, c), penalty, scale)
+    clauses: list = field(default_factory=list)  # (group, (a, b, c), penalty, scale, step)
 
     def add_term(self, group, xmask, zmask, coef):
         self.terms.append((int(group), int(xmask), int(zmask), float(coef)))
 
-    def add_clause(self, group, bits, penalty=PEN_INDICATOR, scale=1.0):
-        self.clauses.append((int(group), tuple(int(b) for b in bits), int(penalty), float(scale)))
+    def add_clause(self, group, bits, penalty=PEN_INDICATOR, scale=1.0, step=0):
+        """step = j >= 1 marks clause h_j of the clause-by-clause sequence (Eq. kpath)."""
+        self.clauses.append((int(group), tuple(int(b) for b in bits), int(penalty), float(scale), int(step)))
 
     def _ctypes(self):
         nt, nc = len(self.terms), len(self.clauses)
@@ -126,6 +129,8 @@ class Hamiltonian:
         keep["cg"] = np.array([c[0] for c in self.clauses] or [0], dtype=np.int32)
         keep["cp"] = np.array([c[2] for c in self.clauses] or [0], dtype=np.int32)
         keep["cs"] = np.array([c[3] for c in self.clauses] or [0.0], dtype=np.float64)
+        keep["st"] = np.array([c[4] for c in self.clauses] or [0], dtype=np.int32)
+        step_m = sum(1 for c in self.clauses if c[4] > 0)
         h = _Ham(
             self.n, nt,
             keep["x"].ctypes.data_as(C.POINTER(C.c_uint64)),
@@ -137,6 +142,8 @@ class Hamiltonian:
             keep["cg"].ctypes.data_as(C.POINTER(C.c_int)),
             keep["cp"].ctypes.data_as(C.POINTER(C.c_int)),
             keep["cs"].ctypes.data_as(C.POINTER(C.c_double)),
+            keep["st"].ctypes.data_as(C.POINTER(C.c_int)),
+            step_m,
         )
         return h, keep
 
@@ -247,6 +254,13 @@ def xy_hamiltonian(inst, driver="xy", penalty=PEN_INDICATOR, catalyst=None):
     return H
 
 
+def add_clause_by_clause(H, clauses, group=2, penalty=PEN_INDICATOR, scale=1.0):
+    """H_d(s) of Eq. kpath over `clauses` in the given order (clause j of the list is h_j);
+    use with a group weight of 1 (Eq. cbc: H = (1-s) H_i + s H_f + H_d(s))."""
+    for j, c in enumerate(clauses):
+        H.add_clause(group, c, penalty, scale, step=j + 1)
+
+
 def ec3_hamiltonian(inst, penalty=PEN_INDICATOR, pairs=None, x_weights=None):
     """The workload Hamiltonian: H_i (group 0), H_f (group 1) and optional H_c (group 2)."""
     H = Hamiltonian(inst.n)
@@ -279,10 +293,14 @@ class Schedule:
                 sc.poly[g][k] = float(self.poly[g][k])
         return sc
 
-    def weights(self, t):
+    def s_of(self, t):
         tau = t / self.T
-        s = tau if self.s_kind == S_LINEAR else 3 * tau * tau - 2 * tau ** 3
-        return [sum(self.poly[g][k] * s ** k for k in range(4)) for g in range(3)]
+        return tau if self.s_kind == S_LINEAR else 3 * tau * tau - 2 * tau ** 3
+
+    def weights(self, t):
+        """[w_A, w_B, w_C, s] at time t (s is used by clause-by-clause sequences)."""
+        s = self.s_of(t)
+        return [sum(self.poly[g][k] * s ** k for k in range(4)) for g in range(3)] + [s]
 
 
 def linear_path(T, s_kind=S_LINEAR):
@@ -293,6 +311,11 @@ def linear_path(T, s_kind=S_LINEAR):
 def nonlinear_path(T, s_kind=S_LINEAR, alpha=1.0):
     """Eq. nlpath form: H(s) = (1 - s) H_i + s H_f + alpha s (1 - s) H_c."""
     return Schedule(T, s_kind, ((1.0, -1.0, 0.0, 0.0), (0.0, 1.0, 0.0, 0.0), (0.0, alpha, -alpha, 0.0)))
+
+
+def clause_by_clause_path(T, s_kind=S_LINEAR):
+    """Eq. cbc: A = 1 - s, B = s, C = 1 (the clause-by-clause term carries its own s-dependence)."""
+    return Schedule(T, s_kind, ((1.0, -1.0, 0.0, 0.0), (0.0, 1.0, 0.0, 0.0), (1.0, 0.0, 0.0, 0.0)))
 
 
 # ----------------------------------------------------------------------------------------
@@ -306,7 +329,7 @@ def hpsi(H: Hamiltonian, weights, psi, nthreads=1):
         raise ValueError("psi must have 2**n entries")
     out = np.zeros_like(psi)
     h, keep = H._ctypes()
-    w = (C.c_double * 3)(*[float(x) for x in weights])
+    w = (C.c_double * 4)(*[float(x) for x in list(weights)[:4]] + [0.0] * (4 - min(4, len(weights))))
     rc = lib.or_hpsi(C.byref(h), w, psi.ctypes.data, out.ctypes.data, int(nthreads))
     if rc != 0:
         raise RuntimeError("or_hpsi failed")
@@ -322,7 +345,7 @@ def hpsi_at(H: Hamiltonian, weights, psi, zs):
     zs = np.ascontiguousarray(zs, dtype=np.uint64)
     out = np.zeros(len(zs), dtype=np.complex128)
     h, keep = H._ctypes()
-    w = (C.c_double * 3)(*[float(x) for x in weights])
+    w = (C.c_double * 4)(*[float(x) for x in list(weights)[:4]] + [0.0] * (4 - min(4, len(weights))))
     rc = lib.or_hpsi_at(C.byref(h), w, psi.ctypes.data, len(zs), zs.ctypes.data, out.ctypes.data)
     if rc != 0:
         raise RuntimeError("or_hpsi_at failed")
@@ -414,8 +437,26 @@ def dense_matrix(H: Hamiltonian, weights):
     M = np.zeros((N, N), dtype=np.complex128)
     for (g, x, z, c) in H.terms:
         M += weights[g] * c * pauli_string_matrix(n, x, z)
-    for (g, bits, pen, scale) in H.clauses:
+    plain = [c for c in H.clauses if c[4] == 0]
+    steps = sorted((c for c in H.clauses if c[4] > 0), key=lambda c: c[4])
+    for (g, bits, pen, scale, _) in plain:
         M += np.diag(weights[g] * scale * clause_diagonal(n, bits, pen))
+    if steps:
+        # Eq. kpath, segment by segment: on s_k in [0, 1), H_d = (1 - s_k) H_{k-1} + s_k H_k with
+        # H_j the first j clauses of the sequence (1 <= j <= m-1) and H_0 = H_m = 0
+        m, s = len(steps), float(weights[3])
+
+        def H_j(j):
+            d = np.zeros(N)
+            if 1 <= j <= m - 1:
+                for (g, bits, pen, scale, _) in steps[:j]:
+                    d += weights[g] * scale * clause_diagonal(n, bits, pen)
+            return d
+
+        k = min(int(math.floor(m * s)) + 1, m)
+        sk = m * s - k + 1
+        if 0.0 <= sk < 1.0:
+            M += np.diag((1.0 - sk) * H_j(k - 1) + sk * H_j(k))
     return M
 
 

@@ -1,0 +1,74 @@
+"""Pins of the oracle's clause-by-clause term H_d(s) (Eq. cbc, Eq. kpath).
+
+The C oracle sums the definition over k with the Theta factors; the checks build H_d from
+explicit partial sums H_j of clause diagonals, segment by segment, and test the properties the
+paper states: H_d(0) = H_d(1) = 0 (H(0) = H^xy, H(1) = H_f), continuity at s = k/m, and on
+s_k in [0, 1) the interpolation (1 - s_k) H_{k-1} + s_k H_k with H_0 = H_m = 0.
+"""
+import numpy as np
+import pytest
+
+from instances import generate_ec3
+from oracle import oracle as O
+
+
+def _diag_of(H, weights):
+    n = H.n
+    return np.array([O.hpsi(H, weights, np.eye(1, 1 << n, z, dtype=np.complex128)[0])[z].real for z in range(1 << n)])
+
+
+def _partial_sum(n, clauses, j, m):
+    d = np.zeros(1 << n)
+    if 1 <= j <= m - 1:
+        for c in clauses[:j]:
+            d += O.clause_diagonal(n, c, O.PEN_INDICATOR)
+    return d
+
+
+@pytest.mark.parametrize("seed", [1, 4])
+def test_segments_interpolate_partial_sums(seed):
+    inst = generate_ec3(7, seed)
+    n, cl = inst.n, list(inst.clauses)
+    m = len(cl)
+    H = O.Hamiltonian(n)
+    O.add_clause_by_clause(H, cl, group=2)
+    for k in range(1, m + 1):
+        for sk in (0.0, 0.3, 0.9):
+            s = (k - 1 + sk) / m
+            got = _diag_of(H, [0.0, 0.0, 1.0, s])
+            ref = (1 - sk) * _partial_sum(n, cl, k - 1, m) + sk * _partial_sum(n, cl, k, m)
+            assert np.max(np.abs(got - ref)) < 1e-12, (k, sk)
+
+
+def test_ends_vanish_and_continuity():
+    inst = generate_ec3(8, 2)
+    n, cl = inst.n, list(inst.clauses)
+    m = len(cl)
+    H = O.Hamiltonian(n)
+    O.add_clause_by_clause(H, cl, group=2)
+    assert np.max(np.abs(_diag_of(H, [0.0, 0.0, 1.0, 0.0]))) == 0.0
+    assert np.max(np.abs(_diag_of(H, [0.0, 0.0, 1.0, 1.0]))) == 0.0
+    for k in range(1, m):
+        a = _diag_of(H, [0.0, 0.0, 1.0, k / m - 1e-12])
+        b = _diag_of(H, [0.0, 0.0, 1.0, k / m])
+        assert np.max(np.abs(a - b)) < 1e-9
+    # the dense builder (segment formula) agrees with the C oracle (sum over k)
+    for s in (0.05, 0.37, 0.5, 0.99):
+        D = O.dense_matrix(H, [0.0, 0.0, 1.0, s])
+        assert np.max(np.abs(np.diag(D).real - _diag_of(H, [0.0, 0.0, 1.0, s]))) < 1e-12
+
+
+def test_cbc_path_from_xy_start_reaches_h_f():
+    """Eq. cbc with the XY driver: H(0) = H^xy and H(1) = H_f exactly (the weights of the
+    oracle's schedule and H_d vanish at the ends)."""
+    inst = generate_ec3(7, 3)
+    n, cl = inst.n, list(inst.clauses)
+    H = O.xy_hamiltonian(inst, driver="xy")
+    O.add_clause_by_clause(H, cl, group=2)
+    sched = O.clause_by_clause_path(10.0)
+    Hxy = O.Hamiltonian(n)
+    O.add_xy_driver(Hxy, cl, 0)
+    Hf = O.Hamiltonian(n)
+    O.add_ec3_clauses(Hf, cl, 1)
+    assert np.max(np.abs(O.dense_matrix(H, sched.weights(0.0)) - O.dense_matrix(Hxy, [1, 0, 0, 0]))) < 1e-12
+    assert np.max(np.abs(O.dense_matrix(H, sched.weights(10.0)) - O.dense_matrix(Hf, [0, 1, 0, 0]))) < 1e-12

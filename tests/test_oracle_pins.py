@@ -377,11 +377,12 @@ def test_c_schedule_weights_closed_form():
     for kind in (0, 1):
         sc = O.nonlinear_path(8.0, kind, alpha=2.0)._ctypes()
         for t in (0.0, 1.0, 2.5, 4.0, 6.5, 8.0):
-            w = (C.c_double * 3)()
+            w = (C.c_double * 4)()
             lib.or_weights(C.byref(sc), t, w)
             tau = t / 8.0
             s = tau if kind == 0 else 3 * tau * tau - 2 * tau ** 3
             assert abs(w[0] - (1 - s)) < 1e-15 and abs(w[1] - s) < 1e-15 and abs(w[2] - 2 * s * (1 - s)) < 1e-15
+            assert abs(w[3] - s) < 1e-15
 
 
 def test_smoothstep_schedule_weights():
