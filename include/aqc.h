@@ -110,7 +110,13 @@ int aqc_load_terms(aqc_ctx *ctx, int group, size_t n_terms, const uint64_t *xmas
 
 /* Append m Exact-Cover-3 clauses (Eq. 1clause) to group `group`: bits[3k..3k+2] are the
  * 0-based bits of clause k (distinct, < n); its diagonal energy on |z> is
- * scale * pen(#ones), pen per `penalty` (AQC_PEN_*; Eq. hci for AQC_PEN_SQUARED). */
+ * scale * pen(#ones), pen per `penalty` (AQC_PEN_*; Eq. hci for AQC_PEN_SQUARED).
+ * penalty | AQC_CLAUSE_STEPWISE makes the m clauses, in the given order, the sequence
+ * h_1..h_m of the clause-by-clause term H_d(s) of Eq. kpath: clause j is further multiplied by
+ * its coefficient in sum_k [(1 - s_k) H_{k-1} + s_k H_k] [0 <= s_k < 1], s_k = m s - k + 1,
+ * H_k = h_1 + ... + h_k, H_0 = H_m = 0 (use a group weight of 1 for Eq. cbc).  One such
+ * sequence per context; contexts holding one cannot join a batch. */
+#define AQC_CLAUSE_STEPWISE 0x100
 int aqc_load_clauses(aqc_ctx *ctx, int group, size_t m, const int32_t *bits, int penalty, double scale);
 
 /* Remove all terms and clauses of all groups. */

@@ -6,13 +6,14 @@ the method's arithmetic (no Hamiltonian construction, no matvec, no integrator):
 builds its own Hamiltonian from these data.
 """
 from .rng import SplitMix64
-from .ec3 import EC3Instance, generate_ec3, count_solutions, xx_pairs
+from .ec3 import EC3Instance, generate_ec3, generate_ec3_hard, count_solutions, xx_pairs
 from .vectors import random_state, uniform_state_value
 
 __all__ = [
     "SplitMix64",
     "EC3Instance",
     "generate_ec3",
+    "generate_ec3_hard",
     "count_solutions",
     "xx_pairs",
     "random_state",

@@ -191,3 +191,58 @@ def xx_pairs(n: int, seed: int, count: int | None = None):
         seen.add(key)
         chosen.append(key)
     return [(i, j, 2.0 * rng.uniform() - 1.0) for (i, j) in chosen]
+
+
+def _pairs(c):
+    a, b, d = c
+    return ((a, b), (a, d), (b, d))
+
+
+def generate_ec3_hard(n: int, seed: int, m_max: int | None = None, max_restarts: int = 10000) -> EC3Instance:
+    """Seeded hard EC3 instance by the recipe of Sec. I.E (Fig. hardEC3): start from one random
+    clause of the full pool; keep drawing at random among the remaining clauses that touch the
+    graph built so far and share no bit pair with it (n_ij in {0, 1}); once every bit is in the
+    graph, count solutions after each draw and discard a clause that leaves none; stop at a
+    unique solution; restart when the pool runs dry or m_max clauses are reached.
+    m_max defaults to ceil(2n/3) + 2 (near the phase transition m ~ 2n/3 the paper aims at)."""
+    if n < 4 or n > 40:
+        raise ValueError("n must be in [4, 40]")
+    if m_max is None:
+        m_max = -(-2 * n // 3) + 2
+    rng = SplitMix64(seed ^ 0x4A5D0C1A55E5)
+    triples = [(a, b, c) for a in range(n) for b in range(a + 1, n) for c in range(b + 1, n)]
+    for restart in range(max_restarts):
+        pool = set(triples)
+        first = triples[rng.below(len(triples))]
+        pool.discard(first)
+        clauses = [first]
+        bits = set(first)
+        used_pairs = set(_pairs(first))
+        while True:
+            # clauses that touch the graph and share no edge with it
+            cand = sorted(c for c in pool if (set(c) & bits) and not (set(_pairs(c)) & used_pairs))
+            if not cand or len(clauses) >= m_max:
+                break  # restart
+            c = cand[rng.below(len(cand))]
+            pool.discard(c)
+            if len(bits) == n:
+                cnt = count_solutions(n, clauses + [c], cap=2)
+                if cnt == 0:
+                    continue  # discard
+                clauses.append(c)
+                used_pairs.update(_pairs(c))
+                if cnt == 1:
+                    w = _solution(n, clauses)
+                    return EC3Instance(n=n, clauses=tuple(clauses), solution=w, seed=seed, restarts=restart)
+            else:
+                clauses.append(c)
+                bits.update(c)
+                used_pairs.update(_pairs(c))
+                if len(bits) == n:
+                    cnt = count_solutions(n, clauses, cap=2)
+                    if cnt == 1:
+                        w = _solution(n, clauses)
+                        return EC3Instance(n=n, clauses=tuple(clauses), solution=w, seed=seed, restarts=restart)
+                    if cnt == 0:
+                        break  # unsatisfiable before any check could discard: restart
+    raise RuntimeError("no hard instance found within the restart limit")

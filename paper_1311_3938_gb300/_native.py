@@ -25,6 +25,7 @@ AQC_C128 = 0
 AQC_C64 = 1
 AQC_GRP_A, AQC_GRP_B, AQC_GRP_C = 0, 1, 2
 AQC_PEN_INDICATOR, AQC_PEN_SQUARED = 0, 1
+AQC_CLAUSE_STEPWISE = 0x100
 AQC_S_LINEAR, AQC_S_SMOOTHSTEP = 0, 1
 AQC_INIT_UNIFORM, AQC_INIT_BASIS, AQC_INIT_USER_HOST, AQC_INIT_USER_DEVICE, AQC_INIT_DICKE = 0, 1, 2, 3, 4
 

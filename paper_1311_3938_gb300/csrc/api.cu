@@ -31,6 +31,7 @@ struct ClauseH {
   uint32_t mask;
   int group, pen;
   double scale;
+  int stepwise;  // member of the clause-by-clause sequence (Eq. kpath)
 };
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -136,6 +137,8 @@ struct aqc_ctx {
   std::vector<char> xpartial;        // layout l's partial pass can run as k_partial_x
   int n_remote = 0, n_z = 0;
   int table_class = -1;
+  int step_class = -1, step_m = 0;  // clause-by-clause sequence (class index, length)
+  double eval_s = 0.0;              // path parameter s of the evaluation being issued
 
   bool have_sched = false;
   int s_kind = 0;
@@ -354,7 +357,9 @@ int build_tables(aqc_ctx* c) {
   for (size_t i = 0; i < cl.size(); i++) {
     int k = -1;
     for (size_t j = 0; j < classes.size(); j++)
-      if (classes[j].group == cl[i].group && classes[j].pen == cl[i].pen && classes[j].scale == cl[i].scale) k = (int)j;
+      if (classes[j].group == cl[i].group && classes[j].pen == cl[i].pen && classes[j].scale == cl[i].scale &&
+          classes[j].stepwise == cl[i].stepwise)
+        k = (int)j;
     if (k < 0) {
       if ((int)classes.size() >= kMaxClasses) FAIL(c, AQC_E_UNSUPPORTED, "more than %d clause classes", kMaxClasses);
       DevClass dc;
@@ -362,6 +367,7 @@ int build_tables(aqc_ctx* c) {
       dc.group = cl[i].group;
       dc.pen = cl[i].pen;
       dc.scale = cl[i].scale;
+      dc.stepwise = cl[i].stepwise;
       classes.push_back(dc);
       k = (int)classes.size() - 1;
     }
@@ -377,13 +383,20 @@ int build_tables(aqc_ctx* c) {
     t->classes[k] = classes[k];
   }
   t->n_classes = (int)classes.size();
-  // cache the counts of clause class 0 as one byte per index when they fit
+  // cache the counts of the first fixed-weight clause class as one byte per index when they fit
   t->table_class = -1;
-  if (!classes.empty()) {
-    const int cnt = classes[0].end - classes[0].begin;
-    const int maxv = classes[0].pen == AQC_PEN_SQUARED ? 4 * cnt : cnt;
-    if (maxv <= 255) t->table_class = 0;
+  c->step_class = -1;
+  for (size_t k = 0; k < classes.size(); k++) {
+    if (classes[k].stepwise) {
+      c->step_class = (int)k;
+      continue;
+    }
+    if (t->table_class >= 0) continue;
+    const int cnt = classes[k].end - classes[k].begin;
+    const int maxv = classes[k].pen == AQC_PEN_SQUARED ? 4 * cnt : cnt;
+    if (maxv <= 255) t->table_class = (int)k;
   }
+  c->step_m = c->step_class >= 0 ? classes[c->step_class].end - classes[c->step_class].begin : 0;
   c->table_class = t->table_class;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_tab, t, sizeof(DevTables), cudaMemcpyHostToDevice, c->stream));
   if (t->table_class >= 0) {
@@ -396,9 +409,15 @@ int build_tables(aqc_ctx* c) {
   return AQC_OK;
 }
 
-void sched_weights(const aqc_ctx* c, double t, double w[3]) {
+double sched_s(const aqc_ctx* c, double t) {
   const double tau = t / c->T;
-  const double s = c->s_kind == AQC_S_SMOOTHSTEP ? tau * tau * (3.0 - 2.0 * tau) : tau;
+  return c->s_kind == AQC_S_SMOOTHSTEP ? tau * tau * (3.0 - 2.0 * tau) : tau;
+}
+
+// Group weights at time t; also records s(t) for the clause-by-clause coefficients.
+void sched_weights(aqc_ctx* c, double t, double w[3]) {
+  const double s = sched_s(c, t);
+  c->eval_s = s;
   for (int g = 0; g < 3; g++) w[g] = ((c->poly[g][3] * s + c->poly[g][2]) * s + c->poly[g][1]) * s + c->poly[g][0];
 }
 
@@ -458,9 +477,28 @@ bool encode_tile_map(CUtensorMap* m, const void* v, int n, const Layout& L) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Coefficients of the clause-by-clause sequence at s (Eq. kpath): on segment k (s_k in [0, 1)),
+// clauses j < k weigh 1 (1 - s_k on the last segment, where H_m = 0), clause k weighs s_k (0 on
+// the last segment), later clauses 0; step_k = 0 outside [0, 1).
+void set_step_fields(const aqc_ctx* c, ApplyParams* p) {
+  p->step_k = 0;
+  p->step_wdone = p->step_wact = 0.0;
+  const int m = c->step_m;
+  const double s = c->eval_s;
+  if (c->step_class < 0 || m < 1 || !(s >= 0.0 && s < 1.0)) return;
+  int k = (int)floor((double)m * s) + 1;
+  if (k > m) k = m;
+  const double sk = (double)m * s - (double)k + 1.0;
+  if (!(sk >= 0.0 && sk < 1.0)) return;
+  p->step_k = k;
+  p->step_wdone = k <= m - 1 ? 1.0 : 1.0 - sk;
+  p->step_wact = k <= m - 1 ? sk : 0.0;
+}
+
 ApplyParams base_params(aqc_ctx* c) {
   ApplyParams p;
   memset(&p, 0, sizeof(p));
+  set_step_fields(c, &p);
   p.tab = c->d_tab;
   p.n = c->n;
   p.partials = c->d_partials;
@@ -898,7 +936,14 @@ int aqc_load_terms(aqc_ctx* ctx, int group, size_t n_terms, const uint64_t* xmas
 int aqc_load_clauses(aqc_ctx* ctx, int group, size_t m, const int32_t* bits, int penalty, double scale) {
   if (!ctx) return AQC_E_INVAL;
   if (group < 0 || group > 2) FAIL(ctx, AQC_E_INVAL, "group must be 0, 1 or 2");
+  const int stepwise = (penalty & AQC_CLAUSE_STEPWISE) ? 1 : 0;
+  penalty &= ~AQC_CLAUSE_STEPWISE;
   if (penalty != AQC_PEN_INDICATOR && penalty != AQC_PEN_SQUARED) FAIL(ctx, AQC_E_INVAL, "bad penalty kind");
+  if (stepwise) {
+    for (const ClauseH& c : ctx->clauses)
+      if (c.stepwise) FAIL(ctx, AQC_E_INVAL, "the context already holds a clause-by-clause sequence");
+    if (m == 0) FAIL(ctx, AQC_E_INVAL, "empty clause-by-clause sequence");
+  }
   if (!isfinite(scale)) FAIL(ctx, AQC_E_INVAL, "non-finite scale");
   if (m && !bits) FAIL(ctx, AQC_E_INVAL, "NULL clause array");
   for (size_t k = 0; k < m; k++) {
@@ -908,7 +953,7 @@ int aqc_load_clauses(aqc_ctx* ctx, int group, size_t m, const int32_t* bits, int
   }
   for (size_t k = 0; k < m; k++) {
     const uint32_t mask = (1u << bits[3 * k]) | (1u << bits[3 * k + 1]) | (1u << bits[3 * k + 2]);
-    ctx->clauses.push_back(ClauseH{mask, group, penalty, scale});
+    ctx->clauses.push_back(ClauseH{mask, group, penalty, scale, stepwise});
   }
   ctx->dirty = true;
   return AQC_OK;
@@ -1127,6 +1172,7 @@ int aqc_energy(aqc_ctx* ctx, int group, double* out) {
   }
   double w[3] = {0.0, 0.0, 0.0};
   w[group] = 1.0;
+  if (ctx->T > 0.0) ctx->eval_s = sched_s(ctx, (double)ctx->step * ctx->h);  // s at the current time
   ApplyParams fin = base_params(ctx);
   fin.mode = MODE_ENERGY;
   int rc = evaluate(ctx, w, ctx->vec[V_Y], fin, nullptr);
@@ -1299,6 +1345,8 @@ int aqc_batch_add(aqc_batch* b, aqc_ctx* c, int* slot_out) {
   if (!b || !c) return AQC_E_INVAL;
   if (c->device != b->device || c->prec != b->prec) BFAIL(b, AQC_E_INVAL, "context device/precision differ from the batch");
   if (!c->have_state) BFAIL(b, AQC_E_STATE, "context has no initial state");
+  for (const ClauseH& k : c->clauses)
+    if (k.stepwise) BFAIL(b, AQC_E_UNSUPPORTED, "clause-by-clause sequences are not batched");
   for (aqc_ctx* m : b->members)
     if (m == c) BFAIL(b, AQC_E_INVAL, "context is already a member");
   int slot = -1;

@@ -42,6 +42,8 @@ struct DevClass {  // clauses [begin, end) share group, penalty and scale
   int32_t group;
   int32_t pen;     // 0 indicator [k != 1], 1 squared (1-k)^2
   int32_t begin, end;
+  int32_t stepwise;  // the clause-by-clause sequence h_1..h_m (Eq. kpath), in order
+  int32_t pad;
   double scale;
 };
 
@@ -117,6 +119,9 @@ struct ApplyParams {
   void* fout;        // STEP: f_{n+1};  DERIV: f;  RK4 stage 1: history f_n
   void* pout;        // STEP: p_{n+2};  RK4: stage input for the next stage (ys)
   void* acc;         // RK4 accumulator
+  int step_k;        // clause-by-clause segment k (0: no clause of the sequence active)
+  double step_wdone; // coefficient of clauses j < k of the sequence
+  double step_wact;  // coefficient of clause k
   double* partials;  // per-CTA reduction partials (3 doubles per CTA)
   unsigned* counter; // last-CTA ticket (reset to 0 by the last CTA)
   double* slots;     // results: see kSlot*

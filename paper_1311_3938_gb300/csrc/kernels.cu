@@ -139,6 +139,22 @@ __device__ bool grid_reduce(double (&v)[K], double* partials, unsigned* counter,
   return false;
 }
 
+// Clause-by-clause sequence (Eq. kpath) on segment k: sum over clauses j <= k of the sequence
+// of pen_j(z), weighted wdone for j < k and wact for j = k.
+template <typename R>
+__device__ __forceinline__ R clause_sum_step(const DevTables* __restrict__ tab, const DevClass& cl, uint32_t z, int k,
+                                             R wdone, R wact) {
+  const int m = cl.end - cl.begin;
+  const int kk = k < m ? k : m;
+  R sum = (R)0;
+  for (int j = 1; j <= kk; j++) {
+    const int ones = __popc(tab->clause_mask[cl.begin + j - 1] & z);
+    const R pen = cl.pen == 0 ? (R)(ones != 1) : (R)((1 - ones) * (1 - ones));
+    sum += (j < k ? wdone : wact) * pen;
+  }
+  return sum;
+}
+
 template <typename R>
 __device__ __forceinline__ R clause_count(const DevTables* __restrict__ tab, const DevClass& cl, uint32_t z) {
   int cnt = 0;
@@ -211,6 +227,8 @@ struct TileCtx {
   uint32_t tsize, tmask;
   int np, npf, ngl, ng, nz, ncls, tcls, stage;
   R dconst, wtab, h;
+  int step_k;          // clause-by-clause segment (0: none active)
+  R step_wdone, step_wact;
   const DevTables* tab;
   const uint8_t* dcode;
   double w0, w1, w2;
@@ -694,7 +712,9 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
         for (int cc = 0; cc < T.ncls; cc++) {
           if (cc == T.tcls) continue;
           const DevClass cl = T.tab->classes[cc];
-          d += (R)(cl.scale * pick3(T.w0, T.w1, T.w2, cl.group)) * clause_count<R>(T.tab, cl, z[g]);
+          const R cnt = cl.stepwise ? clause_sum_step<R>(T.tab, cl, z[g], T.step_k, T.step_wdone, T.step_wact)
+                                    : clause_count<R>(T.tab, cl, z[g]);
+          d += (R)(cl.scale * pick3(T.w0, T.w1, T.w2, cl.group)) * cnt;
         }
         for (int k = 0; k < T.nz; k++) {
           const SZ<R> e = T.s_z[k];
@@ -806,6 +826,9 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_PARTIAL && sizeof(R) =
                        P.w[2], smem);
   T.stage = P.stage;
   T.h = (R)P.h;
+  T.step_k = P.step_k;
+  T.step_wdone = (R)P.step_wdone;
+  T.step_wact = (R)P.step_wact;
   T.src = reinterpret_cast<const C2*>(P.src);
   T.qin = reinterpret_cast<const C2*>(P.qin);
   T.qout = reinterpret_cast<C2*>(P.qout);
@@ -899,6 +922,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_slab(const SlabParams S) {
                        B.w[2], smem, smem + mapA.total);
   TS.stage = TP.stage = 0;
   TS.h = TP.h = (R)A.h;
+  TS.step_k = A.step_k;
+  TS.step_wdone = (R)A.step_wdone;
+  TS.step_wact = (R)A.step_wact;
+  TP.step_k = 0;
+  TP.step_wdone = TP.step_wact = (R)0;
   TS.src = TP.src = reinterpret_cast<const C2*>(A.src);
   TS.qin = reinterpret_cast<const C2*>(A.qin);
   TS.y = reinterpret_cast<C2*>(A.y);
@@ -996,6 +1024,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_batch(BatchLaunc
                        batch_weight(*I, s, 0), batch_weight(*I, s, 1), batch_weight(*I, s, 2), smem);
   T.stage = 0;
   T.h = (R)I->h;
+  T.step_k = 0;  // clause-by-clause sequences are not batched
+  T.step_wdone = T.step_wact = (R)0;
   C2* const* v = reinterpret_cast<C2* const*>(I->vec);
   T.src = v[kVecP];
   T.qin = first ? nullptr : v[kVecQ];

@@ -71,9 +71,11 @@ class Context:
             raise ValueError("term arrays differ in length")
         N.aqc_load_terms(self.handle, group, len(x), x.ctypes.data, z.ctypes.data, c.ctypes.data)
 
-    def load_clauses(self, group, clauses, penalty=N.AQC_PEN_INDICATOR, scale=1.0):
+    def load_clauses(self, group, clauses, penalty=N.AQC_PEN_INDICATOR, scale=1.0, stepwise=False):
+        """EC3 clauses; stepwise=True makes them (in order) the clause-by-clause sequence."""
         b = np.ascontiguousarray(np.asarray(clauses, dtype=np.int32).reshape(-1))
-        N.aqc_load_clauses(self.handle, group, len(b) // 3, b.ctypes.data, penalty, scale)
+        kind = penalty | (N.AQC_CLAUSE_STEPWISE if stepwise else 0)
+        N.aqc_load_clauses(self.handle, group, len(b) // 3, b.ctypes.data, kind, scale)
 
     def clear_hamiltonian(self):
         N.aqc_clear_hamiltonian(self.handle)

@@ -122,16 +122,27 @@ def removable_clauses(n: int, clauses):
     return [k for k in range(len(clauses)) if connected(clauses[:k] + clauses[k + 1:]) or not base]
 
 
+def clause_by_clause_schedule():
+    """Eq. cbc: A = 1 - s, B = s, C = 1 (the sequence in group C carries the s-dependence of
+    Eq. kpath itself)."""
+    return (W_ONE_MINUS_S, W_S, (1.0, 0.0, 0.0, 0.0))
+
+
 def load_xy(ctx, inst, driver: str = "xy", catalyst_alpha: float = 0.0, removed: int = None,
-            penalty=N.AQC_PEN_INDICATOR):
+            penalty=N.AQC_PEN_INDICATOR, clause_by_clause: bool = False):
     """The XY or XYZ algorithm (Sec. III.A.2-3) with optional catalyst (Eq. nlpath): driver in
     group A, H_f clauses in group B and, if catalyst_alpha != 0, H_{m-1} (every clause but
-    `removed`; default: the last removable clause) in group C.  Returns the schedule (use
-    with ctx.set_schedule) and the Hamming weight of the solution (the Dicke start sector)."""
+    `removed`; default: the last removable clause) in group C; or, with clause_by_clause, the
+    clauses in stored order as the sequence of Eq. kpath in group C (Eq. cbc).  Returns the
+    schedule (use with ctx.set_schedule) and the Hamming weight of the solution (the Dicke
+    start sector)."""
     terms = xy_driver_terms(inst.clauses) if driver == "xy" else xyz_driver_terms(inst.clauses)
     ctx.load_terms(N.AQC_GRP_A, *terms)
     ctx.load_clauses(N.AQC_GRP_B, inst.clauses, penalty=penalty)
     sched = linear_schedule()
+    if clause_by_clause:
+        ctx.load_clauses(N.AQC_GRP_C, list(inst.clauses), penalty=penalty, stepwise=True)
+        return clause_by_clause_schedule(), bin(int(inst.solution)).count("1")
     if catalyst_alpha:
         cl = list(inst.clauses)
         if removed is None:

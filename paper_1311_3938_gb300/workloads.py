@@ -20,7 +20,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from instances import SplitMix64, generate_ec3, xx_pairs
+from instances import SplitMix64, generate_ec3, generate_ec3_hard, xx_pairs
 
 from . import _native as N
 from . import hamiltonians as HB
@@ -39,6 +39,7 @@ class Job:
     arrival: float = 0.0
     driver: str = "x"      # "x" (Eq. Hix, start |S>), "xy" / "xyz" (Eq. Hixy / Hixyz, Dicke start)
     alpha: float = 8.0     # catalyst strength of the XY/XYZ nonlinear path (Eq. nlpath)
+    hard: bool = False     # instance by the hard-instance recipe of Sec. I.E
     # filled in when the job is served
     admitted: float = math.nan
     finished: float = math.nan
@@ -66,15 +67,15 @@ class Job:
 _INSTANCE_CACHE = {}
 
 
-def _instance(n, seed):
-    key = (n, seed)
+def _instance(n, seed, hard=False):
+    key = (n, seed, hard)
     if key not in _INSTANCE_CACHE:
-        _INSTANCE_CACHE[key] = generate_ec3(n, seed)
+        _INSTANCE_CACHE[key] = generate_ec3_hard(n, seed) if hard else generate_ec3(n, seed)
     return _INSTANCE_CACHE[key]
 
 
 def make_context(job: Job, device=0, stream=None, tile_bits=0) -> tuple:
-    inst = _instance(job.n, job.seed)
+    inst = _instance(job.n, job.seed, job.hard)
     pairs = xx_pairs(job.n, job.seed) if job.nonlinear else None
     ctx = Context(job.n, job.precision, device=device, stream=stream)
     if tile_bits:
@@ -253,10 +254,10 @@ def run_algorithms(n=13, seed=3, Ts=(2.0, 5.0, 10.0, 20.0, 50.0), precision=N.AQ
     return rows
 
 
-def run_ts_scaling(ns=(6, 8, 10, 12), count=8, seed=5000, drivers=("x", "xy"), precision=N.AQC_C64,
-                   device=0, T_max=512.0):
-    """Median successful runtime T_s (E(T_s)/Omega = 1/2, Sec. III.B) over `count` seeded
-    instances per n and algorithm, each T_s found by batched solves (tsearch.find_Ts)."""
+def run_ts_scaling(ns=(8, 10, 12), count=8, seed=5000, drivers=("x", "xy"), precision=N.AQC_C64,
+                   device=0, T_max=512.0, hard=True):
+    """Median successful runtime T_s (E(T_s)/Omega = 1/2, Sec. III.B) over `count` seeded hard
+    instances (Sec. I.E) per n and algorithm, each T_s found by batched solves (tsearch.find_Ts)."""
     from .tsearch import find_Ts
 
     rows = []
@@ -266,7 +267,7 @@ def run_ts_scaling(ns=(6, 8, 10, 12), count=8, seed=5000, drivers=("x", "xy"), p
             t0 = time.perf_counter()
             for k in range(count):
                 job = Job(jid=k, n=n, seed=seed + 100 * n + k, nonlinear=False, T=1.0, precision=precision,
-                          driver=driver)
+                          driver=driver, hard=hard)
                 r = find_Ts(job, T_lo=1.0, T_hi=64.0, k=8, rtol=1e-2, device=device, T_max=T_max)
                 evals += r["evaluations"]
                 if r["Ts"] is not None:

@@ -91,3 +91,35 @@ def test_xy_n21_first_steps(prec):
     first 10 steps of the XY algorithm with catalyst against the oracle."""
     inst, k, st, psi, ref = _run_xy(21, 4, prec, "xy", 8.0, 10.0, steps=10)
     assert rel_err(psi, ref.psi) < TOL_STATE[prec] * 0.1
+
+
+@pytest.mark.parametrize("prec", [C128, C64])
+def test_clause_by_clause_path_full_solve(prec):
+    """Eq. cbc / Eq. kpath on the XY algorithm at n = 12: the step grid crosses every segment
+    boundary; full solve against the oracle, and H(t) psi at points inside segments."""
+    from paper_1311_3938_gb300 import hamiltonians as HB
+    from paper_1311_3938_gb300.engine import Context
+
+    n, T = 12, 6.0
+    inst = generate_ec3(n, 13)
+    cl = list(inst.clauses)
+    ctx = Context(n, prec)
+    sched_poly, k = HB.load_xy(ctx, inst, driver="xy", clause_by_clause=True)
+    ctx.set_schedule(T, sched_poly)
+    H = O.xy_hamiltonian(inst, driver="xy")
+    O.add_clause_by_clause(H, cl, group=2)
+    sched = O.clause_by_clause_path(T)
+    psi = O.dicke_state(n, k) * (1.0 + 0.5j)
+    dpsi = torch.from_numpy(psi).cuda()
+    m = len(cl)
+    for t in (0.0, T * 0.37 / m, T * (2.5 / m), T * (m - 0.5) / m, T):
+        got = ctx.hpsi(t, dpsi).cpu().numpy()
+        ref = O.hpsi(H, sched.weights(t), dpsi.cpu().numpy().astype(np.complex128))
+        assert rel_err(got, ref) < (1e-13 if prec == C128 else 2e-6), t
+    ctx.set_integrator(0, 0.0)
+    ctx.set_initial_state(("dicke", k))
+    ctx.propagate(-1)
+    got = ctx.state()
+    ctx.close()
+    ref = O.propagate(H, sched, O.step_count(H, sched), O.dicke_state(n, k), nthreads=16)
+    assert rel_err(got, ref.psi) < TOL_STATE[prec]

@@ -51,3 +51,30 @@ def test_random_state_normalised():
     v = random_state(8, 3)
     assert abs(np.vdot(v, v).real - 1) < 1e-14
     assert np.array_equal(v, random_state(8, 3))
+
+
+@pytest.mark.parametrize("n", [8, 10, 12, 14])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_hard_instances_follow_the_recipe(n, seed):
+    """Sec. I.E: unique solution (brute force), n_ij in {0, 1} (clauses share at most one bit),
+    a connected clause graph over all n bits, at most m_max clauses; seeded and deterministic."""
+    from instances.ec3 import generate_ec3_hard
+
+    inst = generate_ec3_hard(n, seed)
+    assert inst == generate_ec3_hard(n, seed)
+    assert inst.m <= -(-2 * n // 3) + 2
+    masks = [(1 << a) | (1 << b) | (1 << c) for (a, b, c) in inst.clauses]
+    sols = [z for z in range(1 << n) if all(bin(z & m).count("1") == 1 for m in masks)]
+    assert sols == [inst.solution]
+    for i in range(len(masks)):
+        for j in range(i + 1, len(masks)):
+            assert bin(masks[i] & masks[j]).count("1") <= 1
+    # connectivity over all bits
+    reach, frontier = set(inst.clauses[0]), True
+    while frontier:
+        frontier = False
+        for c in inst.clauses:
+            if set(c) & reach and not set(c) <= reach:
+                reach |= set(c)
+                frontier = True
+    assert reach == set(range(n))
