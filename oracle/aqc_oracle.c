@@ -103,17 +103,18 @@ static double clause_penalty(int kind, int k) {
 /* Coefficient of clause h_j (1-based) in Eq. kpath:
  *   H_d(s) = sum_{k=1}^{m} [(1 - s_k) H_{k-1} + s_k H_k] Theta(s_k) Theta(1 - s_k),
  *   s_k = m s - k + 1,  H_k = h_1 + ... + h_k (1 <= k <= m-1),  H_0 = H_m = 0.
- * Theta(s_k) Theta(1 - s_k) is read as s_k in [0, 1), so every s lies in one segment. */
+ * Theta(s_k) Theta(1 - s_k) is read as s_k in [0, 1), so every s lies in one segment: the sum
+ * has one nonzero term.  Near a segment end the rounded s_k of two neighbouring segments can
+ * both land in [0, 1); the first (lowest k) is the segment s lies in. */
 static double kpath_coef(int j, int m, double s) {
-  double c = 0.0;
   for (int k = 1; k <= m; k++) {
     double sk = (double)m * s - (double)k + 1.0;
     if (!(sk >= 0.0 && sk < 1.0)) continue;
     int in_prev = (k - 1 >= 1) && (k - 1 <= m - 1) && (j <= k - 1); /* h_j is part of H_{k-1} */
     int in_cur = (k <= m - 1) && (j <= k);                           /* h_j is part of H_k */
-    c += (1.0 - sk) * (double)in_prev + sk * (double)in_cur;
+    return (1.0 - sk) * (double)in_prev + sk * (double)in_cur;
   }
-  return c;
+  return 0.0;
 }
 
 /* weight of clause k of H at the weights w (w[3] = s) */

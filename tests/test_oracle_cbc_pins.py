@@ -72,3 +72,26 @@ def test_cbc_path_from_xy_start_reaches_h_f():
     O.add_ec3_clauses(Hf, cl, 1)
     assert np.max(np.abs(O.dense_matrix(H, sched.weights(0.0)) - O.dense_matrix(Hxy, [1, 0, 0, 0]))) < 1e-12
     assert np.max(np.abs(O.dense_matrix(H, sched.weights(10.0)) - O.dense_matrix(Hf, [0, 1, 0, 0]))) < 1e-12
+
+
+@pytest.mark.parametrize("m,N", [(11, 4620), (7, 2940), (13, 1001)])
+def test_one_segment_on_step_grids(m, N):
+    """On step grids whose points fall on segment ends up to rounding, every clause coefficient
+    stays in [0, 1] and the coefficients match the segment formula (no segment counted twice)."""
+    cl = [(0, 1, 2)] * m
+    H = O.Hamiltonian(3)
+    for j in range(m):
+        H.add_clause(2, (0, 1, 2), O.PEN_INDICATOR, 1.0, step=j + 1)
+    T = 6.0
+    h = T / N
+    for n in range(N + 1):
+        for t in (n * h, n * h + 0.5 * h):
+            s = t / T
+            d = O.hpsi(H, [0.0, 0.0, 1.0, s], np.eye(1, 8, 0, dtype=np.complex128)[0])[0].real  # z = 0: pen 1 each
+            # the segment of s from its integer part; sum of the coefficients of H_d on it
+            k = min(int(np.floor(m * s)) + 1, m)
+            sk = m * s - k + 1
+            ref = 0.0
+            if 0.0 <= s < 1.0:
+                ref = (1 - sk) * (k - 1 if 1 <= k - 1 <= m - 1 else 0) + sk * (k if k <= m - 1 else 0)
+            assert abs(d - ref) < 1e-9, (n, s * m, d, ref)
