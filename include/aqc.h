@@ -148,6 +148,14 @@ int aqc_get_grid(aqc_ctx *ctx, int64_t *n_steps, double *h);
  * Batch members always use per-CTA tiles.  Resets the integrator. */
 int aqc_set_tile_bits(aqc_ctx *ctx, int tile_bits);
 
+/* Qubit relabelling (enable = 1, the default): when products flip several qubits, the library
+ * may store qubit q at another index bit so that as many products as possible lie inside one
+ * tile layout (a product no layout holds costs one extra state-vector read per evaluation).
+ * Transparent to callers: every entry point takes and returns qubit-order indices and vectors
+ * (Eq. ztensor); only the context's device vectors are reordered.  0 keeps the identity order.
+ * A state already set is reordered when the tables are next built. */
+int aqc_set_relabel(aqc_ctx *ctx, int enable);
+
 /* Slab order of a PEC step (one PEC step = the one H*psi evaluation of Sec. I.B plus the
  * corrector/predictor update).  With three or more layouts, the last partial-sum pass and the
  * fused step kernel run as one launch over slabs of the index space (fixed values of up to

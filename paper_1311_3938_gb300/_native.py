@@ -77,6 +77,7 @@ def lib():
             "aqc_set_integrator": (i32, [vp, i64, dbl]),
             "aqc_set_tile_bits": (i32, [vp, i32]),
             "aqc_set_slab_bits": (i32, [vp, i32]),
+            "aqc_set_relabel": (i32, [vp, i32]),
             "aqc_get_grid": (i32, [vp, C.POINTER(i64), C.POINTER(dbl)]),
             "aqc_set_initial_state": (i32, [vp, i32, u64, vp]),
             "aqc_propagate": (i32, [vp, i64, C.POINTER(aqc_stats)]),
@@ -176,6 +177,10 @@ def aqc_get_grid(ctx):
 
 def aqc_set_tile_bits(ctx, tile_bits):
     _check(ctx, lib().aqc_set_tile_bits(ctx, int(tile_bits)))
+
+
+def aqc_set_relabel(ctx, enable):
+    _check(ctx, lib().aqc_set_relabel(ctx, 1 if enable else 0))
 
 
 def aqc_set_slab_bits(ctx, slab_bits):

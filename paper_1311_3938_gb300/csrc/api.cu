@@ -87,7 +87,7 @@ std::vector<Layout> layouts_for(int n, int prec, int tile_bits, bool allow_clust
 
 
 struct WsPlan {
-  size_t off_tab, off_slots, off_counter, off_sync, off_partials, off_dcode, off_vec, vec_bytes, total;
+  size_t off_tab, off_slots, off_counter, off_sync, off_perm, off_partials, off_dcode, off_vec, vec_bytes, total;
   size_t partial_doubles;
 };
 
@@ -98,7 +98,8 @@ WsPlan plan_workspace(int n, int prec) {
   w.off_slots = align_up(sizeof(DevTables), 256);
   w.off_counter = w.off_slots + 256;
   w.off_sync = w.off_counter + 256;  // slab work counter + per-slab counters
-  w.off_partials = w.off_sync + align_up((1 + kMaxSlabs) * sizeof(unsigned), 256);
+  w.off_perm = w.off_sync + align_up((1 + kMaxSlabs) * sizeof(unsigned), 256);  // bit-permutation tables
+  w.off_partials = w.off_perm + 4 * 256 * sizeof(uint32_t);
   // k_apply grids are persistent (at most kMaxApplyGrid CTAs); k_norm2 uses reduce_grid()
   size_t g = std::max((size_t)kMaxApplyGrid, (size_t)reduce_grid((uint64_t)1 << n));
   w.partial_doubles = 3 * g;
@@ -125,6 +126,7 @@ struct aqc_ctx {
   double* d_slots = nullptr;
   unsigned* d_counter = nullptr;
   unsigned* d_sync = nullptr;
+  uint32_t* d_perm = nullptr;
   double* d_partials = nullptr;
   uint8_t* d_dcode = nullptr;
   DevTables* h_tab = nullptr;
@@ -148,6 +150,9 @@ struct aqc_ctx {
   double kappa = 0.1;
   int tile_bits = 0;  // 0: the precision's default
   int slab_req = 0;   // slab bits: 0 off (default), -1 automatic, k > 0 at most k
+  int relabel = 1;    // choose the qubit -> index-bit order that keeps flips inside layouts
+  std::vector<int> perm;  // perm[q] = index bit of qubit q in the library's vectors
+  bool permuted = false;  // perm is not the identity
   SlabParams slab;    // slab-ordered last passes of a PEC step (slab.n_slabs == 0: off)
   bool in_batch = false;  // batch members use per-CTA tiles only
 
@@ -208,6 +213,110 @@ uint32_t compress_mask(const Layout& L, uint32_t x) {
 
 void plan_layouts(aqc_ctx* c) { c->layouts = layouts_for(c->n, c->prec, c->tile_bits, !c->in_batch); }
 
+// ---- qubit relabelling ----------------------------------------------------------------------
+// The library may store qubit q at index bit perm[q] (a relabelling of the tensor factors of
+// Eq. ztensor): a product whose flip mask spans two layouts is gathered from global memory once
+// per evaluation, and most such products can be moved inside one layout by relabelling.  All
+// entry points take and return qubit-order data; only the device vectors are in bit order.
+uint64_t map_bits(const std::vector<int>& perm, uint64_t z) {
+  uint64_t r = 0;
+  for (size_t q = 0; q < perm.size(); q++)
+    if ((z >> q) & 1u) r |= (uint64_t)1 << perm[q];
+  return r;
+}
+
+uint64_t phys_index(const aqc_ctx* c, uint64_t z) { return c->permuted ? map_bits(c->perm, z) : z; }
+
+// dst[z] = src[M(z)], M(z) = map_bits(m, z)
+int permute_gather(aqc_ctx* c, void* dst, const void* src, const std::vector<int>& m) {
+  uint32_t tab[4 * 256];
+  for (int b = 0; b < 4; b++)
+    for (int v = 0; v < 256; v++) {
+      uint32_t r = 0;
+      for (int i = 0; i < 8; i++) {
+        const int q = 8 * b + i;
+        if (((v >> i) & 1) && q < c->n) r |= 1u << m[q];
+      }
+      tab[256 * b + v] = r;
+    }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_perm, tab, sizeof(tab), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, launch_permute(c->prec, dst, src, c->N, c->d_perm, c->stream));
+  c->launches++;
+  return AQC_OK;
+}
+
+std::vector<int> inverse_perm(const std::vector<int>& p) {
+  std::vector<int> r(p.size());
+  for (size_t q = 0; q < p.size(); q++) r[p[q]] = (int)q;
+  return r;
+}
+
+// qubit order -> library order: dst[p] = src[perm^-1(p)]
+int to_library_order(aqc_ctx* c, void* dst, const void* src) { return permute_gather(c, dst, src, inverse_perm(c->perm)); }
+// library order -> qubit order: dst[z] = src[perm(z)]
+int to_qubit_order(aqc_ctx* c, void* dst, const void* src) { return permute_gather(c, dst, src, c->perm); }
+
+// Order that minimises the products (weighted by how many share a flip mask) that no layout
+// holds: deterministic local search over transpositions, kept only if strictly better than the
+// identity.
+std::vector<int> choose_order(const aqc_ctx* c) {
+  std::vector<int> id(c->n);
+  for (int q = 0; q < c->n; q++) id[q] = q;
+  if (!c->relabel || c->layouts.size() < 2) return id;
+  std::vector<std::pair<uint32_t, int>> masks;  // distinct multi-bit flip masks with counts
+  for (const TermH& th : c->terms) {
+    if (__builtin_popcount(th.x) < 2) continue;
+    bool found = false;
+    for (auto& m : masks)
+      if (m.first == th.x) {
+        m.second++;
+        found = true;
+      }
+    if (!found) masks.push_back({th.x, 1});
+  }
+  if (masks.empty()) return id;
+  std::vector<uint32_t> lm;
+  for (const Layout& L : c->layouts) lm.push_back(layout_mask(L));
+  auto cost = [&](const std::vector<int>& p) {
+    int k = 0;
+    for (const auto& m : masks) {
+      const uint32_t x = (uint32_t)map_bits(p, m.first);
+      bool held = false;
+      for (uint32_t l : lm) held = held || (x & ~l) == 0;
+      if (!held) k += m.second;
+    }
+    return k;
+  };
+  const int c0 = cost(id);
+  if (c0 == 0) return id;
+  std::vector<int> cur = id, best = id;
+  int ccur = c0, cbest = c0;
+  uint64_t st = 0x9E3779B97F4A7C15ull;  // SplitMix64 stream
+  auto next = [&]() {
+    st += 0x9E3779B97F4A7C15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  for (int it = 0; it < 20000 && cbest > 0; it++) {
+    const int a = (int)(next() % (uint64_t)c->n), b = (int)(next() % (uint64_t)c->n);
+    if (a == b) continue;
+    std::swap(cur[a], cur[b]);
+    const int cn = cost(cur);
+    if (cn <= ccur || (next() & 63u) == 0u) {
+      ccur = cn;
+      if (cn < cbest) {
+        cbest = cn;
+        best = cur;
+      }
+    } else {
+      std::swap(cur[a], cur[b]);
+    }
+  }
+  return cbest < c0 ? best : id;
+}
+
 int popcount32(uint32_t v) { return __builtin_popcount(v); }
 
 // Slab order for the last two passes of a PEC step (SlabParams): needs three or more layouts
@@ -267,7 +376,35 @@ int build_tables(aqc_ctx* c) {
   t->n_layouts = nl;
   std::vector<std::vector<DevFlip>> per(nl + 1);
   int nz = 0;
-  for (const TermH& th : c->terms) {
+  // qubit order of the library's vectors; a state already set moves to the new order
+  {
+    std::vector<int> np = choose_order(c);
+    std::vector<int> old = c->perm.empty() ? std::vector<int>() : c->perm;
+    if (old.empty()) {
+      old.resize(c->n);
+      for (int q = 0; q < c->n; q++) old[q] = q;
+    }
+    if (np != old && c->have_state) {
+      // new[p] = old[old_perm(new_perm^-1(p))]
+      const std::vector<int> inv = inverse_perm(np);
+      std::vector<int> m(c->n);
+      for (int p = 0; p < c->n; p++) m[p] = old[inv[p]];
+      const int live[] = {V_Y, V_P, V_F0, V_F0 + 1, V_F0 + 2, V_F0 + 3};
+      for (int v : live) {
+        int rc = permute_gather(c, c->vec[V_ACC], c->vec[v], m);
+        if (rc) return rc;
+        CUDA_TRY(c, cudaMemcpyAsync(c->vec[v], c->vec[V_ACC], (size_t)c->N * c->amp, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+      }
+    }
+    c->perm = np;
+    c->permuted = false;
+    for (int q = 0; q < c->n; q++) c->permuted = c->permuted || np[q] != q;
+  }
+  for (const TermH& th0 : c->terms) {
+    TermH th = th0;
+    th.x = (uint32_t)phys_index(c, th0.x);
+    th.zm = (uint32_t)phys_index(c, th0.zm);
     if (th.x == 0) {
       if (th.zm == 0) {
         t->ident[th.group] += th.coef;
@@ -378,7 +515,7 @@ int build_tables(aqc_ctx* c) {
   for (size_t k = 0; k < classes.size(); k++) {
     classes[k].begin = cp;
     for (size_t i = 0; i < cl.size(); i++)
-      if (cls_of[i] == (int)k) t->clause_mask[cp++] = cl[i].mask;
+      if (cls_of[i] == (int)k) t->clause_mask[cp++] = (uint32_t)phys_index(c, cl[i].mask);
     classes[k].end = cp;
     t->classes[k] = classes[k];
   }
@@ -889,6 +1026,7 @@ int aqc_create(aqc_ctx** out, int device, int precision, int n_qubits, void* wor
   c->d_slots = (double*)(c->ws + wp.off_slots);
   c->d_counter = (unsigned*)(c->ws + wp.off_counter);
   c->d_sync = (unsigned*)(c->ws + wp.off_sync);
+  c->d_perm = (uint32_t*)(c->ws + wp.off_perm);
   c->d_partials = (double*)(c->ws + wp.off_partials);
   c->d_dcode = (uint8_t*)(c->ws + wp.off_dcode);
   for (int v = 0; v < V_COUNT; v++) c->vec[v] = c->ws + wp.off_vec + (size_t)v * wp.vec_bytes;
@@ -998,6 +1136,13 @@ int aqc_set_tile_bits(aqc_ctx* ctx, int tile_bits) {
   return AQC_OK;
 }
 
+int aqc_set_relabel(aqc_ctx* ctx, int enable) {
+  if (!ctx) return AQC_E_INVAL;
+  ctx->relabel = enable ? 1 : 0;
+  ctx->dirty = true;  // a state already set moves to the new order at the next table build
+  return AQC_OK;
+}
+
 int aqc_set_slab_bits(aqc_ctx* ctx, int slab_bits) {
   if (!ctx) return AQC_E_INVAL;
   if (slab_bits < -1 || slab_bits > 11) FAIL(ctx, AQC_E_INVAL, "slab_bits must be -1, 0 or 1..11");
@@ -1028,6 +1173,11 @@ int aqc_get_grid(aqc_ctx* ctx, int64_t* n_steps, double* h) {
 int aqc_set_initial_state(aqc_ctx* ctx, int kind, uint64_t basis, const void* user) {
   if (!ctx) return AQC_E_INVAL;
   DeviceGuard dg(ctx->device);
+  if (ctx->dirty) {  // the qubit order of the vectors must be known
+    ctx->have_state = false;
+    int rc = build_tables(ctx);
+    if (rc) return rc;
+  }
   void* y = ctx->vec[V_Y];
   const size_t bytes = (size_t)ctx->N * ctx->amp;
   switch (kind) {
@@ -1037,7 +1187,7 @@ int aqc_set_initial_state(aqc_ctx* ctx, int kind, uint64_t basis, const void* us
       break;
     case AQC_INIT_BASIS:
       if (basis >= ctx->N) FAIL(ctx, AQC_E_INVAL, "basis index >= 2^n");
-      CUDA_TRY(ctx, launch_init(ctx->prec, y, ctx->N, 1, basis, 0.0, ctx->stream));
+      CUDA_TRY(ctx, launch_init(ctx->prec, y, ctx->N, 1, phys_index(ctx, basis), 0.0, ctx->stream));
       ctx->launches++;
       break;
     case AQC_INIT_DICKE: {
@@ -1050,11 +1200,21 @@ int aqc_set_initial_state(aqc_ctx* ctx, int kind, uint64_t basis, const void* us
     }
     case AQC_INIT_USER_HOST:
       if (!user) FAIL(ctx, AQC_E_INVAL, "user vector is NULL");
-      CUDA_TRY(ctx, cudaMemcpyAsync(y, user, bytes, cudaMemcpyHostToDevice, ctx->stream));
+      CUDA_TRY(ctx, cudaMemcpyAsync(ctx->permuted ? ctx->vec[V_ACC] : y, user, bytes, cudaMemcpyHostToDevice,
+                                    ctx->stream));
+      if (ctx->permuted) {
+        int rc = to_library_order(ctx, y, ctx->vec[V_ACC]);
+        if (rc) return rc;
+      }
       break;
     case AQC_INIT_USER_DEVICE:
       if (!user) FAIL(ctx, AQC_E_INVAL, "user vector is NULL");
-      CUDA_TRY(ctx, cudaMemcpyAsync(y, user, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      if (ctx->permuted) {
+        int rc = to_library_order(ctx, y, user);
+        if (rc) return rc;
+      } else {
+        CUDA_TRY(ctx, cudaMemcpyAsync(y, user, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      }
       break;
     default:
       FAIL(ctx, AQC_E_INVAL, "bad initial-state kind");
@@ -1147,8 +1307,15 @@ int aqc_get_state(aqc_ctx* ctx, void* dst, int dst_on_device) {
   if (!ctx) return AQC_E_INVAL;
   if (!dst) FAIL(ctx, AQC_E_INVAL, "dst is NULL");
   DeviceGuard dg(ctx->device);
-  CUDA_TRY(ctx, cudaMemcpyAsync(dst, ctx->vec[V_Y], (size_t)ctx->N * ctx->amp,
-                                dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  const void* src = ctx->vec[V_Y];
+  if (ctx->permuted) {  // back to qubit order: on the device directly, or via the scratch vector
+    int rc = to_qubit_order(ctx, dst_on_device ? dst : ctx->vec[V_ACC], ctx->vec[V_Y]);
+    if (rc) return rc;
+    src = ctx->vec[V_ACC];
+  }
+  if (!(ctx->permuted && dst_on_device))
+    CUDA_TRY(ctx, cudaMemcpyAsync(dst, src, (size_t)ctx->N * ctx->amp,
+                                  dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return AQC_OK;
 }
@@ -1157,7 +1324,7 @@ int aqc_fidelity(aqc_ctx* ctx, uint64_t w, double* out) {
   if (!ctx || !out) return AQC_E_INVAL;
   if (w >= ctx->N) FAIL(ctx, AQC_E_INVAL, "w >= 2^n");
   DeviceGuard dg(ctx->device);
-  CUDA_TRY(ctx, launch_fidelity(ctx->prec, ctx->vec[V_Y], w, ctx->d_slots, ctx->stream));
+  CUDA_TRY(ctx, launch_fidelity(ctx->prec, ctx->vec[V_Y], phys_index(ctx, w), ctx->d_slots, ctx->stream));
   ctx->launches++;
   return read_slot(ctx, kSlotDot, out);
 }
@@ -1258,7 +1425,15 @@ int aqc_hpsi(aqc_ctx* ctx, double t, const void* psi, void* out) {
   sched_weights(ctx, t, w);
   ApplyParams fin = base_params(ctx);
   fin.mode = MODE_PARTIAL;
-  return evaluate(ctx, w, psi, fin, out);
+  if (!ctx->permuted) return evaluate(ctx, w, psi, fin, out);
+  // qubit order in and out: psi -> scratch (library order) -> H psi into out -> qubit order
+  int rc = to_library_order(ctx, ctx->vec[V_ACC], psi);
+  if (!rc) rc = evaluate(ctx, w, ctx->vec[V_ACC], fin, out);
+  if (!rc) rc = to_qubit_order(ctx, ctx->vec[V_ACC], out);
+  if (rc) return rc;
+  CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->vec[V_ACC], (size_t)ctx->N * ctx->amp, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+  return AQC_OK;
 }
 
 
@@ -1512,7 +1687,12 @@ int aqc_lanczos(aqc_ctx* ctx, double t, const void* start, void* work, size_t wo
   cudaStream_t s = ctx->stream;
   const uint64_t N = ctx->N;
   // v_0 = start / ||start||
-  CUDA_TRY(ctx, cudaMemcpyAsync(V(0), start, N * ctx->amp, cudaMemcpyDeviceToDevice, s));
+  if (ctx->permuted) {
+    int rc = to_library_order(ctx, V(0), start);
+    if (rc) return rc;
+  } else {
+    CUDA_TRY(ctx, cudaMemcpyAsync(V(0), start, N * ctx->amp, cudaMemcpyDeviceToDevice, s));
+  }
   CUDA_TRY(ctx, launch_dotc_multi(ctx->prec, V(0), ld, 1, V(0), N, partials, scal, nullptr, s));
   CUDA_TRY(ctx, launch_scale_to(ctx->prec, V(0), V(0), N, scal, s));
   ctx->launches += 3;

@@ -237,6 +237,7 @@ cudaError_t launch_sub_multi(int prec, void* w, const void* V, uint64_t ld, uint
 cudaError_t launch_scale_to(int prec, void* v, const void* w, uint64_t N, const double* nrm2, cudaStream_t s);
 cudaError_t launch_diag_codes(uint8_t* out, uint64_t N, const DevTables* tab, int cls, cudaStream_t s);
 cudaError_t launch_init(int prec, void* y, uint64_t N, int kind, uint64_t basis, double amp, cudaStream_t s);
+cudaError_t launch_permute(int prec, void* dst, const void* src, uint64_t N, const uint32_t* tab, cudaStream_t s);
 cudaError_t launch_predict(int prec, void* p, const void* y, const void* f3, const void* f2, const void* f1,
                            const void* f0, double h, uint64_t N, cudaStream_t s);
 cudaError_t launch_reduce(int prec, int what, const void* a, uint64_t N, double* partials, unsigned* counter,

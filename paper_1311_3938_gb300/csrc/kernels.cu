@@ -1285,6 +1285,31 @@ cudaError_t launch_init(int prec, void* y, uint64_t N, int kind, uint64_t basis,
   return cudaGetLastError();
 }
 
+// dst[z] = src[M(z)] for a permutation M of the index bits, M(z) = OR_b tab[b][byte b of z]
+// (qubit relabelling: the state lives in the library's bit order, callers see qubit order)
+template <typename R>
+__global__ void k_permute_bits(typename Cplx<R>::T* __restrict__ dst, const typename Cplx<R>::T* __restrict__ src,
+                               uint64_t N, const uint32_t* __restrict__ tab) {
+  __shared__ uint32_t s_tab[4 * 256];
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s_tab[i] = tab[i];
+  __syncthreads();
+  for (uint64_t z = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; z < N; z += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t zz = (uint32_t)z;
+    const uint32_t m = s_tab[zz & 255u] | s_tab[256 + ((zz >> 8) & 255u)] | s_tab[512 + ((zz >> 16) & 255u)] |
+                       s_tab[768 + (zz >> 24)];
+    dst[z] = src[m];
+  }
+}
+
+cudaError_t launch_permute(int prec, void* dst, const void* src, uint64_t N, const uint32_t* tab, cudaStream_t s) {
+  const int grid = (int)((N + 255) / 256 < 4096 ? (N + 255) / 256 : 4096);
+  if (prec == 0)
+    k_permute_bits<double><<<grid, 256, 0, s>>>((double2*)dst, (const double2*)src, N, tab);
+  else
+    k_permute_bits<float><<<grid, 256, 0, s>>>((float2*)dst, (const float2*)src, N, tab);
+  return cudaGetLastError();
+}
+
 // p_{n+1} = y_n + h/24 (55 f_n - 59 f_{n-1} + 37 f_{n-2} - 9 f_{n-3})   (AB4 predictor)
 template <typename R>
 __global__ void k_predict(typename Cplx<R>::T* p, const typename Cplx<R>::T* y, const typename Cplx<R>::T* f3,

@@ -91,6 +91,10 @@ class Context:
     def set_tile_bits(self, tile_bits=0):
         N.aqc_set_tile_bits(self.handle, tile_bits)
 
+    def set_relabel(self, enable=True):
+        """Qubit relabelling that keeps multi-qubit flips inside tile layouts (transparent)."""
+        N.aqc_set_relabel(self.handle, enable)
+
     def set_slab_bits(self, slab_bits=0):
         """Slab order of the PEC step: 0 off, -1 automatic, k > 0 at most k slab bits."""
         N.aqc_set_slab_bits(self.handle, slab_bits)
