@@ -238,6 +238,35 @@ def run_sequential(jobs, device=0, keep_state=False):
     return time.perf_counter() - t0
 
 
+def run_batch512(count=512, seed=1000, device=0, sample_every=16):
+    """The batched workload at full size: `count` instances from `seed`, n ~ U{12..22}, nonlinear
+    path, T ~ U[10, 200], complex64, all as members of one batch (autotuned shape).  One-at-a-time
+    solves of every job would take hours, so the comparison runs on every `sample_every`-th job:
+    batched and sequential on that sample, equal step grids."""
+    import copy
+
+    from . import autotune as A
+
+    jobs = random_jobs(count, seed, n_range=(12, 22), T_range=(10.0, 200.0), nonlinear=True)
+    shape, _ = A.autotune(jobs[:16], rounds=3)
+    tile_bits, threads, spr = shape
+    t_all = run_batched(jobs, device, threads=threads, steps_per_round=spr, tile_bits=tile_bits)
+    sample = [copy.deepcopy(j) for j in jobs[::sample_every]]
+    sb = copy.deepcopy(sample)
+    t_sb = run_batched(sb, device, threads=threads, steps_per_round=spr, tile_bits=tile_bits)
+    t_ss = run_sequential(sample, device)
+    amp_steps = sum(j.steps * (1 << j.n) for j in jobs)
+    return {"workload": f"{count} EC3 instances, seeds {seed}-{seed + count - 1}, n~U{{12..22}}, nonlinear, "
+                        "T~U[10,200], complex64",
+            "grid_steps_total": sum(j.steps for j in jobs), "amplitude_steps": amp_steps,
+            "wall_s_batched": t_all, "solves_per_s_batched": count / t_all,
+            "alg_GBs_batched": 7 * 8 * amp_steps / t_all / 1e9,
+            "sample": len(sample), "sample_wall_s_batched": t_sb, "sample_wall_s_sequential": t_ss,
+            "sample_speedup": t_ss / t_sb,
+            "sample_max_abs_dP1": max(abs(a.P1 - b.P1) for a, b in zip(sb, sample)),
+            "autotuned_shape": {"tile_bits": tile_bits, "threads": threads, "steps_per_round": spr}}
+
+
 def run_algorithms(n=13, seed=3, Ts=(2.0, 5.0, 10.0, 20.0, 50.0), precision=N.AQC_C64, device=0):
     """The algorithms of Sec. III-IV on one instance: X (from |S>), XYZ and XY (from the Dicke
     state of the solution's weight), and XY with the alpha = 8 catalyst (Eq. nlpath), each over
@@ -320,7 +349,7 @@ def _main():
     import json
 
     ap = argparse.ArgumentParser(description="workload drivers")
-    ap.add_argument("what", choices=["sweep20", "algorithms", "ts", "gap"])
+    ap.add_argument("what", choices=["sweep20", "algorithms", "ts", "gap", "batch512"])
     ap.add_argument("--n", type=int, default=13)
     a = ap.parse_args()
     if a.what == "sweep20":
@@ -335,6 +364,8 @@ def _main():
     elif a.what == "gap":
         for row in run_gap_curves(n=a.n):
             print(json.dumps(row), flush=True)
+    elif a.what == "batch512":
+        print(json.dumps(run_batch512()), flush=True)
 
 
 class Server:
