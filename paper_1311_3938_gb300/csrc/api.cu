@@ -136,6 +136,7 @@ struct aqc_ctx {
   bool dirty = true;
   std::vector<Layout> layouts;
   std::vector<int> nplain, ngeneral;  // local X-string / general products per layout
+  std::vector<int> nhop;              // of the general ones, the hops (leading)
   std::vector<char> xpartial;        // layout l's partial pass can run as k_partial_x
   int n_remote = 0, n_z = 0;
   int table_class = -1;
@@ -450,6 +451,7 @@ int build_tables(aqc_ctx* c) {
   int pos = 0;
   c->nplain.assign(nl, 0);
   c->ngeneral.assign(nl, 0);
+  c->nhop.assign(nl, 0);
   c->xpartial.assign(nl, 0);
   for (int l = 0; l <= nl; l++) {
     t->flip_begin[l] = pos;
@@ -465,19 +467,32 @@ int build_tables(aqc_ctx* c) {
       for (const DevFlip& f : per[l])
         if (f.zm == 0 && !f.has2 && (f.lx & regbits) != 0) t->flips[pos + np++] = f;
     }
-    int k = np;
-    for (const DevFlip& f : per[l])
-      if (l == nl || f.zm != 0 || f.has2) t->flips[pos + k++] = f;
+    // general range: hops first (the kernels' hop loop), then the other general products
+    auto is_hop = [](const DevFlip& f) {
+      return f.has2 && f.zm == 0 && f.zm2 == f.x && (f.ipow2 & 3) == 2 && f.group2 == f.group &&
+             f.coef2 == f.coef && __builtin_popcount(f.x) == 2;
+    };
+    int k = np, nh = 0;
+    if (l < nl) {
+      for (const DevFlip& f : per[l])
+        if (is_hop(f)) t->flips[pos + k++] = f;
+      nh = k - np;
+      for (const DevFlip& f : per[l])
+        if ((f.zm != 0 || f.has2) && !is_hop(f)) t->flips[pos + k++] = f;
+    } else {
+      for (const DevFlip& f : per[l]) t->flips[pos + k++] = f;
+    }
+    t->hop_count[l] = nh;
     t->plain_count[l] = np;
     t->plain_fast[l] = nfast;
     if (l < nl) {
       c->nplain[l] = np;
       c->ngeneral[l] = (int)per[l].size() - np;
+      c->nhop[l] = nh;
     }
-    if (l > 0 && l < nl) {
-      bool ok = c->prec == AQC_C64 && xpartial_layout_ok(c->layouts[l]) && c->ngeneral[l] == 0 &&
-                xpartial_smem_bytes(np) <= 227 * 1024;
-      for (const DevFlip& f : per[l]) ok = ok && (f.lx & 1u) == 0u;  // pairs stay together
+    if (l > 0 && l < nl) {  // X strings and hops only: the TMA-fed partial kernel
+      const bool ok = c->prec == AQC_C64 && xpartial_layout_ok(c->layouts[l]) && c->ngeneral[l] == nh &&
+                      xpartial_smem_bytes(np + nh) <= 227 * 1024;
       c->xpartial[l] = ok ? 1 : 0;
     }
     pos += (int)per[l].size();
@@ -684,7 +699,7 @@ int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, vo
         x.qout = p.qout;
         x.ntiles = p.ntiles;
         x.slots = c->d_slots;
-        CUDA_TRY(c, launch_partial_x(x, (int)xpartial_smem_bytes(c->nplain[l]), c->stream));
+        CUDA_TRY(c, launch_partial_x(x, (int)xpartial_smem_bytes(c->nplain[l] + c->nhop[l]), c->stream));
         c->launches++;
         continue;
       }

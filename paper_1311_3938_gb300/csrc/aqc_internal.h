@@ -77,6 +77,9 @@ struct DevTables {
   int flip_begin[kMaxLayouts + 2];  // layout l: [flip_begin[l], flip_begin[l+1]); remote after
   int plain_count[kMaxLayouts + 2]; // leading X-string products (zm = 0, real) of each range
   int plain_fast[kMaxLayouts + 2];  // of those, the leading ones that flip no register-held tile bit
+  int hop_count[kMaxLayouts + 2];   // leading entries of the general range that are hops:
+                                    // X_iX_j + Y_iY_j with one real coefficient c, i.e.
+                                    // 2c psi(z ^ x) where bits i, j of z differ, else 0
   int n_z;
   int n_classes;
   int table_class;                  // clause class whose counts are in the per-index byte table, or -1

@@ -225,7 +225,7 @@ struct TileCtx {
   using C2 = typename Cplx<R>::T;
   Layout L;
   uint32_t tsize, tmask;
-  int np, npf, ngl, ng, nz, ncls, tcls, stage;
+  int np, npf, nh, ngl, ng, nz, ncls, tcls, stage;
   R dconst, wtab, h;
   int step_k;          // clause-by-clause segment (0: none active)
   R step_wdone, step_wact;
@@ -261,6 +261,7 @@ __device__ __forceinline__ void load_coefficients(TileCtx<R>& T, const DevTables
   const int fb = tab->flip_begin[li];
   T.np = tab->plain_count[li];
   T.npf = tab->plain_fast[li];
+  T.nh = tab->hop_count[li];
   T.ngl = tab->flip_begin[li + 1] - fb - T.np;
   const int rb = tab->flip_begin[tab->n_layouts];
   const int nrem = with_remote ? tab->n_remote : 0;
@@ -671,8 +672,22 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
         ai[g] += f.c * u[g].y;
       }
     }
-    // 3. general products (Y/Z phases, complex coefficients) and remote products
-    for (int kk = 0; kk < T.ng; kk++) {
+    // 3a. hops X_iX_j + Y_iY_j: 2c psi(z ^ x) where the two bits of z differ (companion
+    //     coefficient c2 = -c after the i^2 phase, so cr - cr2 = 2c)
+    for (int kk = 0; kk < T.nh; kk++) {
+      const SFlip<R> f = T.s_gf[kk];
+      C2 u[G];
+      gather(f.lx, u);
+      const R c2 = f.cr - f.cr2;
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        const R c = (__popc(f.x & z[g]) & 1) ? c2 : (R)0;
+        ar[g] += c * u[g].x;
+        ai[g] += c * u[g].y;
+      }
+    }
+    // 3b. general products (Y/Z phases, complex coefficients) and remote products
+    for (int kk = T.nh; kk < T.ng; kk++) {
       const SFlip<R> f = T.s_gf[kk];
       C2 u[G];
       if (kk < T.ngl) {

@@ -1,7 +1,8 @@
 // Partial-sum pass over a strided tile layout whose products are all X strings with real
-// coefficients (the driver term of Eq. Hix and the XX couplings of the nonlinear path),
-// complex64 only:  q_out(z) = q_in(z) + sum_k c_k psi(z ^ x_k)  for every z of the tile
-// (gather form of the per-qubit action, Sec. I.A).
+// coefficients (the driver term of Eq. Hix and the XX couplings of the nonlinear path) or hops
+// X_iX_j + Y_iY_j (Eq. Hixy), complex64 only:
+//   q_out(z) = q_in(z) + sum_k c_k [hop_k: bits i_k, j_k of z differ] psi(z ^ x_k)
+// for every z of the tile (gather form of the per-qubit action, Sec. I.A).
 //
 // GB300 structure: one CTA of 512 threads per SM, persistent over tiles.  The 64 KiB source
 // tile (2^13 amplitudes) is brought into shared memory by one TMA tensor copy
@@ -29,6 +30,8 @@ constexpr uint32_t kXWaitPolls = 1u << 24;                     // mbarrier polls
 struct XFlip {
   uint32_t lx;
   float c;
+  uint32_t par;  // hops: the flip mask, whose bits must differ in z; 0 for X strings
+  uint32_t pad;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -78,6 +81,18 @@ __device__ __forceinline__ void fma4(float4& a, float c, const float4& g) {
   a.w = fmaf(c, g.w, a.w);
 }
 
+// per-pair coefficients: (c, c) for X strings; for hops c where the two bits of the output
+// index differ, else 0 (cm[r] bit 0 / bit 1: first / second amplitude of pair r qualifies)
+__device__ __forceinline__ void fma4m(float4& a, float c, uint32_t m, const float4& g) {
+  const float c0 = (m & 1u) ? c : 0.f, c1 = (m & 2u) ? c : 0.f;
+  a.x = fmaf(c0, g.x, a.x);
+  a.y = fmaf(c0, g.y, a.y);
+  a.z = fmaf(c1, g.z, a.z);
+  a.w = fmaf(c1, g.w, a.w);
+}
+
+__device__ __forceinline__ float4 swap_pair(const float4& g) { return make_float4(g.z, g.w, g.x, g.y); }
+
 // products flipping register positions only: acc[r] += c * own[r ^ RB]
 template <int RB>
 __device__ __forceinline__ void reg_flip(float c, const float4 (&own)[8], float4 (&acc)[8]) {
@@ -85,11 +100,31 @@ __device__ __forceinline__ void reg_flip(float c, const float4 (&own)[8], float4
   for (int r = 0; r < 8; r++) fma4(acc[r], c, own[r ^ RB]);
 }
 
-// other products: acc[r] += c * tile[(jw ^ sx) | ((r ^ RB) << 6)], row = tile + (jw ^ sx) * 8
-template <int RB>
+// other products: acc[r] += c * tile[(jw ^ sx) | ((r ^ RB) << 6)], row = tile + (jw ^ (sx & ~1)) * 8;
+// SW: the flip includes the pair bit (tile bit 0), so the two amplitudes of a pair trade places
+template <int RB, bool SW>
 __device__ __forceinline__ void smem_flip(float c, const unsigned char* row, float4 (&acc)[8]) {
 #pragma unroll
-  for (int r = 0; r < 8; r++) fma4(acc[r], c, *reinterpret_cast<const float4*>(row + ((r ^ RB) << 9)));
+  for (int r = 0; r < 8; r++) {
+    const float4 g = *reinterpret_cast<const float4*>(row + ((r ^ RB) << 9));
+    fma4(acc[r], c, SW ? swap_pair(g) : g);
+  }
+}
+
+// hops: the same with the per-pair masks of qualifying amplitudes
+template <int RB, bool SW>
+__device__ __forceinline__ void smem_hop(float c, const unsigned char* row, const uint32_t (&cm)[8],
+                                         float4 (&acc)[8]) {
+#pragma unroll
+  for (int r = 0; r < 8; r++) {
+    const float4 g = *reinterpret_cast<const float4*>(row + ((r ^ RB) << 9));
+    fma4m(acc[r], c, cm[r], SW ? swap_pair(g) : g);
+  }
+}
+template <int RB>
+__device__ __forceinline__ void reg_hop(float c, const float4 (&own)[8], const uint32_t (&cm)[8], float4 (&acc)[8]) {
+#pragma unroll
+  for (int r = 0; r < 8; r++) fma4m(acc[r], c, cm[r], own[r ^ RB]);
 }
 
 __device__ __forceinline__ double weight_of(const XPartialParams& P, int g) {
@@ -104,14 +139,16 @@ __global__ void __launch_bounds__(kXThreads, 1) k_partial_x(const __grid_constan
   unsigned char* const buf1 = base + kXTileBytes;
   const DevTables* tab = P.tab;
   const int fb = tab->flip_begin[P.layout_index];
-  const int np = tab->plain_count[P.layout_index];
+  const int np = tab->plain_count[P.layout_index] + tab->hop_count[P.layout_index];  // X strings, then hops
+  const int npl = tab->plain_count[P.layout_index];
   XFlip* s_f = reinterpret_cast<XFlip*>(base + 2 * kXTileBytes);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(base + 2 * kXTileBytes + ((np * sizeof(XFlip) + 15) & ~(size_t)15));
   const uint32_t bar0 = smem_addr(s_bar), bar1 = smem_addr(s_bar + 1);
   const uint32_t tid = threadIdx.x;
   for (int k = tid; k < np; k += blockDim.x) {
     const DevFlip d = tab->flips[fb + k];
-    s_f[k] = XFlip{d.lx, (float)(d.coef * weight_of(P, d.group))};
+    const bool hop = k >= npl;  // X_iX_j + Y_iY_j: 2c where the bits differ
+    s_f[k] = XFlip{d.lx, (float)((hop ? 2.0 : 1.0) * d.coef * weight_of(P, d.group)), hop ? d.x : 0u, 0u};
   }
   if (tid == 0) {
     mbar_init(bar0, 1);
@@ -166,6 +203,48 @@ __global__ void __launch_bounds__(kXThreads, 1) k_partial_x(const __grid_constan
     for (int kk = 0; kk < np; kk++) {
       const XFlip f = s_f[kk];
       const uint32_t rb = (f.lx & kXRegMask) >> 6, sx = f.lx & ~kXRegMask;
+      if (f.par) {  // hop: which output amplitudes have differing bits at the flip mask
+        uint32_t cm[8];
+        const uint32_t pb = __popc(zb & f.par) & 1u;
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+          const uint32_t p0 = pb ^ (__popc(zoff[r] & f.par) & 1u), p1 = p0 ^ (f.par & 1u);
+          cm[r] = p0 | (p1 << 1);
+        }
+        if (sx == 0u) {
+          switch (rb) {
+            case 1: reg_hop<1>(f.c, own, cm, acc); break;
+            case 2: reg_hop<2>(f.c, own, cm, acc); break;
+            case 3: reg_hop<3>(f.c, own, cm, acc); break;
+            case 4: reg_hop<4>(f.c, own, cm, acc); break;
+            case 5: reg_hop<5>(f.c, own, cm, acc); break;
+            case 6: reg_hop<6>(f.c, own, cm, acc); break;
+            default: reg_hop<7>(f.c, own, cm, acc); break;
+          }
+        } else {
+          const unsigned char* row = t + ((jw ^ (sx & ~1u)) << 3);
+          const bool sw = (sx & 1u) != 0u;
+          switch (rb | (sw ? 8u : 0u)) {
+            case 0: smem_hop<0, false>(f.c, row, cm, acc); break;
+            case 1: smem_hop<1, false>(f.c, row, cm, acc); break;
+            case 2: smem_hop<2, false>(f.c, row, cm, acc); break;
+            case 3: smem_hop<3, false>(f.c, row, cm, acc); break;
+            case 4: smem_hop<4, false>(f.c, row, cm, acc); break;
+            case 5: smem_hop<5, false>(f.c, row, cm, acc); break;
+            case 6: smem_hop<6, false>(f.c, row, cm, acc); break;
+            case 7: smem_hop<7, false>(f.c, row, cm, acc); break;
+            case 8: smem_hop<0, true>(f.c, row, cm, acc); break;
+            case 9: smem_hop<1, true>(f.c, row, cm, acc); break;
+            case 10: smem_hop<2, true>(f.c, row, cm, acc); break;
+            case 11: smem_hop<3, true>(f.c, row, cm, acc); break;
+            case 12: smem_hop<4, true>(f.c, row, cm, acc); break;
+            case 13: smem_hop<5, true>(f.c, row, cm, acc); break;
+            case 14: smem_hop<6, true>(f.c, row, cm, acc); break;
+            default: smem_hop<7, true>(f.c, row, cm, acc); break;
+          }
+        }
+        continue;
+      }
       if (sx == 0u) {
         switch (rb) {
           case 1: reg_flip<1>(f.c, own, acc); break;
@@ -177,16 +256,25 @@ __global__ void __launch_bounds__(kXThreads, 1) k_partial_x(const __grid_constan
           default: reg_flip<7>(f.c, own, acc); break;
         }
       } else {
-        const unsigned char* row = t + ((jw ^ sx) << 3);
-        switch (rb) {
-          case 0: smem_flip<0>(f.c, row, acc); break;
-          case 1: smem_flip<1>(f.c, row, acc); break;
-          case 2: smem_flip<2>(f.c, row, acc); break;
-          case 3: smem_flip<3>(f.c, row, acc); break;
-          case 4: smem_flip<4>(f.c, row, acc); break;
-          case 5: smem_flip<5>(f.c, row, acc); break;
-          case 6: smem_flip<6>(f.c, row, acc); break;
-          default: smem_flip<7>(f.c, row, acc); break;
+        const unsigned char* row = t + ((jw ^ (sx & ~1u)) << 3);
+        const bool sw = (sx & 1u) != 0u;
+        switch (rb | (sw ? 8u : 0u)) {
+          case 0: smem_flip<0, false>(f.c, row, acc); break;
+          case 1: smem_flip<1, false>(f.c, row, acc); break;
+          case 2: smem_flip<2, false>(f.c, row, acc); break;
+          case 3: smem_flip<3, false>(f.c, row, acc); break;
+          case 4: smem_flip<4, false>(f.c, row, acc); break;
+          case 5: smem_flip<5, false>(f.c, row, acc); break;
+          case 6: smem_flip<6, false>(f.c, row, acc); break;
+          case 7: smem_flip<7, false>(f.c, row, acc); break;
+          case 8: smem_flip<0, true>(f.c, row, acc); break;
+          case 9: smem_flip<1, true>(f.c, row, acc); break;
+          case 10: smem_flip<2, true>(f.c, row, acc); break;
+          case 11: smem_flip<3, true>(f.c, row, acc); break;
+          case 12: smem_flip<4, true>(f.c, row, acc); break;
+          case 13: smem_flip<5, true>(f.c, row, acc); break;
+          case 14: smem_flip<6, true>(f.c, row, acc); break;
+          default: smem_flip<7, true>(f.c, row, acc); break;
         }
       }
     }

@@ -155,3 +155,42 @@ def test_x_string_partial_passes_sampled(n):
     ref = O.hpsi_at(H, O.Schedule(10.0, 0, poly).weights(3.3), used, zs)
     got = out[zs.astype(np.int64)]
     assert np.max(np.abs(got - ref)) < 2e-6 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,relabel", [(22, False), (27, False), (27, True)])
+def test_hop_partial_passes_sampled(n, relabel):
+    """Hops X_iX_j + Y_iY_j (Eq. Hixy) on pairs inside strided layouts (with and without the
+    pair bit and the register-held tile bits), across layouts, plus an X driver: H(t) psi at
+    sampled outputs against the oracle's single-output evaluation; the TMA-fed partial kernel
+    runs the strided layouts that hold only X strings and hops."""
+    from paper_1311_3938_gb300.engine import Context
+
+    rng = np.random.default_rng(100 + n)
+    H = O.Hamiltonian(n)
+    ctx = Context(n, C64)
+    ctx.set_relabel(relabel)
+    xs, zs, cs = [0], [0], [0.25 * n]
+    for q in range(n):
+        xs.append(1 << q); zs.append(0); cs.append(-0.5)
+    for (a, b) in [(0, 13), (1, 14), (13, 19), (14, 15), (16, 20), (0, 21), (2, n - 1), (21, 22), (n - 2, n - 1),
+                   (5, 17), (3, 9), (0, 5)]:
+        c = float(rng.uniform(-1.0, -0.2))
+        m = (1 << a) | (1 << b)
+        xs += [m, m]; zs += [0, m]; cs += [c, c]
+    for x, z, c in zip(xs, zs, cs):
+        H.add_term(0, x, z, c)
+    ctx.load_terms(0, xs, zs, cs)
+    ctx.load_terms(1, [0], [(1 << 3) | (1 << (n - 1))], [0.3])
+    H.add_term(1, 0, (1 << 3) | (1 << (n - 1)), 0.3)
+    poly = ((1, -1, 0, 0), (0, 1, 0, 0), (0, 0, 0, 0))
+    ctx.set_schedule(10.0, poly, 0)
+    psi = random_state(n, 7 + n)
+    dpsi = torch.from_numpy(psi).to(torch.complex64).cuda()
+    out = ctx.hpsi(2.7, dpsi).cpu().numpy()
+    used = dpsi.cpu().numpy().astype(np.complex128)
+    del dpsi
+    ctx.close()
+    zs_ = _sample_indices(n, 4321, seed=n, count=3000)
+    ref = O.hpsi_at(H, O.Schedule(10.0, 0, poly).weights(2.7), used, zs_)
+    got = out[zs_.astype(np.int64)]
+    assert np.max(np.abs(got - ref)) < 2e-6 * np.abs(ref).max()
