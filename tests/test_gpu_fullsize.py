@@ -174,6 +174,8 @@ def test_hop_partial_passes_sampled(n, relabel):
         xs.append(1 << q); zs.append(0); cs.append(-0.5)
     for (a, b) in [(0, 13), (1, 14), (13, 19), (14, 15), (16, 20), (0, 21), (2, n - 1), (21, 22), (n - 2, n - 1),
                    (5, 17), (3, 9), (0, 5)]:
+        if not (a < n and b < n):
+            continue
         c = float(rng.uniform(-1.0, -0.2))
         m = (1 << a) | (1 << b)
         xs += [m, m]; zs += [0, m]; cs += [c, c]
