@@ -614,19 +614,30 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// A complex64 vector of 2^n amplitudes as a 4-D float tensor whose box is one tile of layout L:
-// (2^(c+1) floats of the contiguous chunk, 2^(h-c) gap positions, 2^w tile rows, top bits).
-bool encode_tile_map(CUtensorMap* m, const void* v, int n, const Layout& L) {
+// A complex64 vector of 2^n amplitudes as a float tensor whose box is one tile of layout L:
+// 4-D (2^(c+1) floats of the contiguous chunk, 2^(h-c) gap positions, 2^w tile rows, top bits)
+// while the chunk fits one box row (c <= 7), else 5-D with the chunk as 256 x 2^(c-7) floats.
+// Returns the rank, or 0 if no map can be made.
+int encode_tile_map(CUtensorMap* m, const void* v, int n, const Layout& L) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc || ((uintptr_t)v & 15u)) return false;
-  const cuuint64_t dims[4] = {(cuuint64_t)2 << L.c, (cuuint64_t)1 << (L.h - L.c), (cuuint64_t)1 << L.w,
+  if (!enc || ((uintptr_t)v & 15u)) return 0;
+  const cuuint32_t es[5] = {1u, 1u, 1u, 1u, 1u};
+  if (L.c <= 7) {
+    const cuuint64_t dims[4] = {(cuuint64_t)2 << L.c, (cuuint64_t)1 << (L.h - L.c), (cuuint64_t)1 << L.w,
+                                (cuuint64_t)1 << (n - L.h - L.w)};
+    const cuuint64_t strides[3] = {(cuuint64_t)8 << L.c, (cuuint64_t)8 << L.h, (cuuint64_t)8 << (L.h + L.w)};
+    const cuuint32_t box[4] = {(cuuint32_t)2 << L.c, 1u, (cuuint32_t)1 << L.w, 1u};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(v), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS ? 4 : 0;
+  }
+  const cuuint64_t dims[5] = {256u, (cuuint64_t)1 << (L.c - 7), (cuuint64_t)1 << (L.h - L.c), (cuuint64_t)1 << L.w,
                               (cuuint64_t)1 << (n - L.h - L.w)};
-  const cuuint64_t strides[3] = {(cuuint64_t)8 << L.c, (cuuint64_t)8 << L.h, (cuuint64_t)8 << (L.h + L.w)};
-  const cuuint32_t box[4] = {(cuuint32_t)2 << L.c, 1u, (cuuint32_t)1 << L.w, 1u};
-  const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(v), dims, strides, box, es,
+  const cuuint64_t strides[4] = {1024u, (cuuint64_t)8 << L.c, (cuuint64_t)8 << L.h, (cuuint64_t)8 << (L.h + L.w)};
+  const cuuint32_t box[5] = {256u, (cuuint32_t)1 << (L.c - 7), 1u, (cuuint32_t)1 << L.w, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(v), dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS ? 5 : 0;
 }
 
 // Coefficients of the clause-by-clause sequence at s (Eq. kpath): on segment k (s_k in [0, 1)),
@@ -690,7 +701,8 @@ int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, vo
     if (!last && !diag && c->xpartial[l] && !(first && c->n_remote > 0)) {
       XPartialParams x;
       memset(&x, 0, sizeof(x));
-      if (encode_tile_map(&x.tmap, src, c->n, p.L)) {
+      x.tma_rank = encode_tile_map(&x.tmap, src, c->n, p.L);
+      if (x.tma_rank) {
         x.tab = c->d_tab;
         x.L = p.L;
         x.layout_index = l;

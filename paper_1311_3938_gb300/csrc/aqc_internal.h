@@ -157,7 +157,9 @@ constexpr int kMaxSlabs = 2048;
 // (complex64, kernel k_partial_x): the source tile arrives by TMA through `tmap`.
 constexpr int kXTileBits = 13;
 struct XPartialParams {
-  CUtensorMap tmap;      // source as a 4-D float tensor (chunk, gap bits, tile rows, top bits)
+  CUtensorMap tmap;      // source as a 4-D float tensor (chunk, gap bits, tile rows, top bits),
+                         // 5-D when the chunk exceeds one box row (chunk split in two dims)
+  int tma_rank;          // 4 or 5
   const DevTables* tab;
   Layout L;
   int layout_index;

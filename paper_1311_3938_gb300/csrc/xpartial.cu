@@ -74,6 +74,15 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2,
+                                            int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+
 __device__ __forceinline__ void fma4(float4& a, float c, const float4& g) {
   a.x = fmaf(c, g.x, a.x);
   a.y = fmaf(c, g.y, a.y);
@@ -171,7 +180,10 @@ __global__ void __launch_bounds__(kXThreads, 1) k_partial_x(const __grid_constan
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     const uint32_t bb = b ? bar1 : bar0;
     mbar_expect_tx(bb, kXTileBytes);
-    tma_load_4d(smem_addr(b ? buf1 : buf0), &P.tmap, bb, 0, x1, 0, x3);
+    if (P.tma_rank == 5)
+      tma_load_5d(smem_addr(b ? buf1 : buf0), &P.tmap, bb, 0, 0, x1, 0, x3);
+    else
+      tma_load_4d(smem_addr(b ? buf1 : buf0), &P.tmap, bb, 0, x1, 0, x3);
   };
   if (tid == 0) {
     if (first < ntiles) issue(first, 0);
@@ -295,8 +307,9 @@ __global__ void __launch_bounds__(kXThreads, 1) k_partial_x(const __grid_constan
 }  // namespace
 
 bool xpartial_layout_ok(const Layout& L) {
-  // TMA box: inner 2^(c+1) floats <= 256, 2^w rows <= 256; tile of 2^13 amplitudes with a gap
-  return L.cb == 0 && L.t == kXTileBits && L.c >= 1 && L.c <= 7 && L.w >= 1 && L.w <= 8 && L.h > L.c;
+  // TMA box: the chunk as 2^(c+1) floats (one box row up to c = 7, else 256 x 2^(c-7)), 2^w <= 256
+  // rows; a strided tile of 2^13 amplitudes
+  return L.cb == 0 && L.t == kXTileBits && L.c >= 1 && L.c <= 12 && L.w >= 1 && L.w <= 8 && L.h > L.c;
 }
 
 size_t xpartial_smem_bytes(int n_flips) {
