@@ -372,7 +372,8 @@ class Server:
     """Continuous-batching request loop (see the module docstring)."""
 
     def __init__(self, precision=N.AQC_C64, device=0, hbm_budget=None, reserve=2 << 30, batch_max_n=22,
-                 max_members=256, threads=256, steps_per_round=16, big_chunk=64, keep_state=False):
+                 max_members=256, threads=256, steps_per_round=16, big_chunk=64, keep_state=False,
+                 big_first=False):
         self.precision = precision
         self.device = device
         free, total = torch.cuda.mem_get_info(device)
@@ -383,11 +384,13 @@ class Server:
         self.keep_state = keep_state
         max_items = max_members * (1 << max(0, batch_max_n - 13 + 2)) + 1024
         # the batch (many short jobs) runs on a high-priority stream, large jobs on low-priority
-        # streams, so CTAs of batch rounds are scheduled first whenever SMs free up
+        # streams, so CTAs of batch rounds are scheduled first whenever SMs free up; big_first
+        # swaps the two (large jobs finish sooner, the batch yields while they run)
         lo, hi = torch.cuda.Stream.priority_range()
-        self.hi_prio, self.lo_prio = hi, lo
+        self.hi_prio, self.lo_prio = (lo, hi) if big_first else (hi, lo)
         self.batch = Batch(precision, device=device, max_members=max_members, max_items=max_items, threads=threads,
-                           steps_per_round=steps_per_round, stream=torch.cuda.Stream(device, priority=hi))
+                           steps_per_round=steps_per_round,
+                           stream=torch.cuda.Stream(device, priority=self.hi_prio))
         self.used = 0
         self.peak_used = 0
         self.occupancy = []
