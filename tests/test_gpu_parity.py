@@ -349,3 +349,30 @@ def test_slab_bits_argument_checks():
     ctx.set_slab_bits(0)
     ctx.set_slab_bits(-1)
     ctx.close()
+
+
+def test_error_codes_of_the_path_extensions():
+    """Argument checks of the Dicke start, clause-by-clause sequences, batches, Lanczos."""
+    from paper_1311_3938_gb300 import _native as N
+    from paper_1311_3938_gb300.engine import Batch
+
+    ctx = _ctx(8, C128)
+    with pytest.raises(N.AqcError) as e:
+        ctx.set_initial_state(("dicke", 9))  # weight > n
+    assert e.value.code == N.AQC_E_INVAL
+    ctx.load_clauses(2, [(0, 1, 2), (3, 4, 5)], stepwise=True)
+    with pytest.raises(N.AqcError) as e:
+        ctx.load_clauses(2, [(1, 2, 3)], stepwise=True)  # one sequence per context
+    assert e.value.code == N.AQC_E_INVAL
+    ctx.set_schedule(1.0, ((1, -1, 0, 0), (0, 1, 0, 0), (1, 0, 0, 0)))
+    ctx.set_initial_state("uniform")
+    b = Batch(C128, max_members=2, max_items=64)
+    with pytest.raises(N.AqcError) as e:
+        b.add(ctx)  # stepwise sequences are not batched
+    assert e.value.code == N.AQC_E_UNSUPPORTED
+    b.close()
+    start = torch.ones(1 << 8, dtype=torch.complex128, device="cuda")
+    for bad in ((0, 1), (5, 6)):  # max_iter < 1; n_eig > max_iter
+        with pytest.raises(N.AqcError) as e:
+            ctx.lanczos(0.5, start, max_iter=bad[0], n_eig=bad[1])
+    ctx.close()
