@@ -476,7 +476,7 @@ def run_ours(a):
             "bound": "hbm",
             "kernel": ("fused PEC step, per grid step: k_apply partial pass(es) + k_slab (last partial layout "
                        "and step over L2-sized slabs)" if a.slab_bits != 0 else
-                       "fused PEC step, per grid step: k_apply partial layouts + MODE_STEP"),
+                       "fused PEC step, per grid step: k_partial_x (TMA) partial passes + k_apply MODE_STEP"),
             "achieved": r64["pec_step_gbs"],
             "peak": hbm_peak,
             "peak_kind": peak_kind,
