@@ -8,7 +8,9 @@ from ._native import (  # noqa: F401
     AQC_GRP_A,
     AQC_GRP_B,
     AQC_GRP_C,
+    AQC_CLAUSE_STEPWISE,
     AQC_INIT_BASIS,
+    AQC_INIT_DICKE,
     AQC_INIT_UNIFORM,
     AQC_PEN_INDICATOR,
     AQC_PEN_SQUARED,
