@@ -91,9 +91,9 @@ def len_layouts(n, t, c):
     return 1 + -(-(n - t) // (t - c))
 
 
-def profiled_traffic(prec_name):
+def profiled_traffic(prec_name, n=N_QUBITS):
     """dram bytes per PEC step from the committed ncu summary, if it was taken on the current
-    kernel sources (else None)."""
+    kernel sources and the same state size (else None)."""
     p = os.path.join(ROOT, "profiles", "pec_step_traffic.json")
     if not os.path.exists(p):
         return None
@@ -102,7 +102,7 @@ def profiled_traffic(prec_name):
     except Exception:
         return None
     e = d.get(prec_name)
-    if not e or e.get("kernel_hash") != kernel_hash():
+    if not e or e.get("kernel_hash") != kernel_hash() or e.get("n", N_QUBITS) != n:
         return None
     return e.get("dram_bytes_per_pec_step")
 
@@ -448,7 +448,7 @@ def run_ours(a):
         if dist is not None:
             dist.destroy_process_group()
         return
-    traffic = profiled_traffic("c64")
+    traffic = profiled_traffic("c64", n)
     line = {
         "metric": METRIC,
         "value": r64["value"],
@@ -518,7 +518,7 @@ def run_ours(a):
                 "unit": "TFLOP/s",
                 "frac": flops / (r128["pec_step_ms"] * 1e-3) / 1e12 / 1.25,
                 "hbm_frac": r128["pec_step_gbs"] / hbm_peak,
-                "traffic": profiled_traffic("c128"),
+                "traffic": profiled_traffic("c128", n),
             },
             "e2e": r128.get("e2e"),
             "gpu_launches": r128["launches"],
