@@ -402,25 +402,35 @@ def run_ours(a):
             "clocks": clocks,
             "matvec_ms": mv_ms,
         }
-        # end-to-end through the public API with host buffers
+        # end-to-end through the public API with pinned host buffers: each step's psi(0) is
+        # copied in and its final psi copied out by the staged transfers, so the copies of
+        # instance k+1 (in) and k (out) overlap the integration; the first copy in and the last
+        # copy out are inside the timed region and not hidden
         if not a.no_e2e:
-            host_in = torch.empty(1 << n, dtype=torch.complex64 if amp == 8 else torch.complex128).pin_memory()
-            host_in.fill_(1.0 / math.sqrt(1 << n))
-            host_out = torch.empty_like(host_in).pin_memory()
+            tdt = torch.complex64 if amp == 8 else torch.complex128
+            host_in = [torch.empty(1 << n, dtype=tdt).pin_memory() for _ in range(2)]
+            for h_ in host_in:
+                h_.fill_(1.0 / math.sqrt(1 << n))
+            host_out = [torch.empty_like(host_in[0]).pin_memory() for _ in range(2)]
+            ctx.attach_transfers()
+            obs = []
 
-            def e2e_step():
-                ctx.set_initial_state(host_in)  # H2D inside the call
-                ctx.propagate(a.pec + 3, stats=False)
-                ctx.fidelity(inst.solution)
-                ctx.energy(P.AQC_GRP_B)
-                ctx.state_into(host_out)  # D2H inside the call
+            def e2e_run(k_steps):
+                ctx.stage_initial_state(host_in[0])
+                for k in range(k_steps):
+                    ctx.set_initial_state("staged")
+                    if k + 1 < k_steps:
+                        ctx.stage_initial_state(host_in[(k + 1) % 2])
+                    ctx.propagate(a.pec + 3, stats=False)
+                    obs.append((ctx.fidelity(inst.solution), ctx.energy(P.AQC_GRP_B)))  # D2H 16 B
+                    ctx.fetch_state(host_out[k % 2])
+                ctx.transfer_wait()
 
-            e2e_step()
+            e2e_run(1)
             torch.cuda.synchronize()
             barrier()
             t0 = time.perf_counter()
-            for _ in range(a.steps):
-                e2e_step()
+            e2e_run(a.steps)
             torch.cuda.synchronize()
             dt = max_over_ranks(time.perf_counter() - t0)
             out["e2e"] = {
@@ -428,7 +438,9 @@ def run_ours(a):
                 "unit": "GB/s",
                 "h2d_bytes_per_step": (1 << n) * amp,
                 "d2h_bytes_per_step": (1 << n) * amp + 16,
+                "copies": "staged (copy engines overlap the integration; first in / last out exposed)",
             }
+            ctx.transfer_wait()
             del host_in, host_out
         ctx.close()
         del ctx

@@ -63,6 +63,7 @@ extern "C" {
 #define AQC_INIT_USER_HOST 2   /* copy of a host vector (state precision, interleaved)   */
 #define AQC_INIT_USER_DEVICE 3 /* copy of a device vector (state precision, interleaved) */
 #define AQC_INIT_DICKE 4       /* C(n,k)^{-1/2} sum_{|u|=k} |u>, k = `basis` (Eq. initstate)  */
+#define AQC_INIT_STAGED 5      /* the vector of the last aqc_stage_initial_state              */
 
 typedef struct aqc_ctx aqc_ctx;
 
@@ -174,7 +175,9 @@ int aqc_set_slab_bits(aqc_ctx *ctx, int slab_bits);
  * AQC_INIT_BASIS and the Hamming weight k (0..n) for AQC_INIT_DICKE (the balanced superposition
  * of all basis states with k one-bits, the ground state of Eq. Hixyz in that sector);
  * `user` points to 2^n interleaved amplitudes in the state precision (host or device memory
- * per the kind).  Out-of-range index or weight: AQC_E_INVAL. */
+ * per the kind).  AQC_INIT_STAGED takes the vector of the last aqc_stage_initial_state (the
+ * context stream waits for its copy; none pending: AQC_E_STATE).  Out-of-range index or
+ * weight: AQC_E_INVAL. */
 int aqc_set_initial_state(aqc_ctx *ctx, int kind, uint64_t basis, const void *user);
 
 /* Advance by up to max_steps grid steps (max_steps < 0: to t = T).  The first three steps
@@ -186,6 +189,35 @@ int aqc_propagate(aqc_ctx *ctx, int64_t max_steps, aqc_stats *stats);
 /* Copy psi to dst (2^n interleaved amplitudes in the state precision); dst is device
  * memory if dst_on_device, else host memory (pinned memory recommended). */
 int aqc_get_state(aqc_ctx *ctx, void *dst, int dst_on_device);
+
+/* ---- staged host transfers ------------------------------------------------------------
+ * Copy-engine transfers that overlap the integrator: the next instance's psi(0) travels to
+ * the device, and the last instance's final psi (Sec. II.B's result) back to the host, while
+ * the context stream integrates.  The caller owns two device staging vectors of 2^n
+ * amplitudes each in the state precision (256-byte aligned, outside the workspace); the
+ * library owns two copy streams and the events that order them against the context stream.  Host buffers should be pinned:
+ * from pageable memory the copies are correct but do not overlap. */
+
+/* Attach the staging vectors (device pointers, each 2^n amplitudes; distinct) and create the
+ * copy streams.  Calling it again replaces the vectors after all pending copies finished.
+ * NULL or misaligned vectors: AQC_E_INVAL; a failed stream or event creation: AQC_E_CUDA. */
+int aqc_transfer_attach(aqc_ctx *ctx, void *stage_in, void *stage_out);
+
+/* Enqueue the copy of 2^n host amplitudes (qubit order, state precision) into the input
+ * staging vector, on the input copy stream, after the previous staged vector was consumed by
+ * aqc_set_initial_state(AQC_INIT_STAGED).  Returns at once; `host_src` must stay unchanged
+ * until aqc_transfer_wait returns or the context stream has passed the consuming
+ * aqc_set_initial_state.  No aqc_transfer_attach: AQC_E_STATE. */
+int aqc_stage_initial_state(aqc_ctx *ctx, const void *host_src);
+
+/* Enqueue on the context stream the copy of psi (qubit order) into the output staging vector,
+ * after the previous fetch left it, then on the output copy stream its copy into 2^n host
+ * amplitudes at `host_dst`.  Returns at once; `host_dst` holds psi once aqc_transfer_wait
+ * returns.  No aqc_transfer_attach: AQC_E_STATE. */
+int aqc_fetch_state(aqc_ctx *ctx, void *host_dst);
+
+/* Block the host until every staged copy and fetch issued so far has completed. */
+int aqc_transfer_wait(aqc_ctx *ctx);
 
 /* |<w|psi>|^2, the success probability P_1 of the solution w (Sec. II.B). */
 int aqc_fidelity(aqc_ctx *ctx, uint64_t w, double *out);

@@ -11,6 +11,7 @@ from ._native import (  # noqa: F401
     AQC_CLAUSE_STEPWISE,
     AQC_INIT_BASIS,
     AQC_INIT_DICKE,
+    AQC_INIT_STAGED,
     AQC_INIT_UNIFORM,
     AQC_PEN_INDICATOR,
     AQC_PEN_SQUARED,

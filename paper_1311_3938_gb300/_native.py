@@ -28,6 +28,7 @@ AQC_PEN_INDICATOR, AQC_PEN_SQUARED = 0, 1
 AQC_CLAUSE_STEPWISE = 0x100
 AQC_S_LINEAR, AQC_S_SMOOTHSTEP = 0, 1
 AQC_INIT_UNIFORM, AQC_INIT_BASIS, AQC_INIT_USER_HOST, AQC_INIT_USER_DEVICE, AQC_INIT_DICKE = 0, 1, 2, 3, 4
+AQC_INIT_STAGED = 5
 
 
 class AqcError(RuntimeError):
@@ -82,6 +83,10 @@ def lib():
             "aqc_set_initial_state": (i32, [vp, i32, u64, vp]),
             "aqc_propagate": (i32, [vp, i64, C.POINTER(aqc_stats)]),
             "aqc_get_state": (i32, [vp, vp, i32]),
+            "aqc_transfer_attach": (i32, [vp, vp, vp]),
+            "aqc_stage_initial_state": (i32, [vp, vp]),
+            "aqc_fetch_state": (i32, [vp, vp]),
+            "aqc_transfer_wait": (i32, [vp]),
             "aqc_fidelity": (i32, [vp, u64, C.POINTER(dbl)]),
             "aqc_energy": (i32, [vp, i32, C.POINTER(dbl)]),
             "aqc_norm2": (i32, [vp, C.POINTER(dbl)]),
@@ -199,6 +204,22 @@ def aqc_propagate(ctx, max_steps, want_stats=True):
 
 def aqc_get_state(ctx, dst_ptr, dst_on_device):
     _check(ctx, lib().aqc_get_state(ctx, C.c_void_p(dst_ptr), int(dst_on_device)))
+
+
+def aqc_transfer_attach(ctx, stage_in_ptr, stage_out_ptr):
+    _check(ctx, lib().aqc_transfer_attach(ctx, C.c_void_p(stage_in_ptr), C.c_void_p(stage_out_ptr)))
+
+
+def aqc_stage_initial_state(ctx, host_ptr):
+    _check(ctx, lib().aqc_stage_initial_state(ctx, C.c_void_p(host_ptr)))
+
+
+def aqc_fetch_state(ctx, host_ptr):
+    _check(ctx, lib().aqc_fetch_state(ctx, C.c_void_p(host_ptr)))
+
+
+def aqc_transfer_wait(ctx):
+    _check(ctx, lib().aqc_transfer_wait(ctx))
 
 
 def aqc_fidelity(ctx, w):

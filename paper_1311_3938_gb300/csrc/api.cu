@@ -157,6 +157,15 @@ struct aqc_ctx {
   SlabParams slab;    // slab-ordered last passes of a PEC step (slab.n_slabs == 0: off)
   bool in_batch = false;  // batch members use per-CTA tiles only
 
+  // staged host transfers (aqc_transfer_attach): caller-owned staging vectors, library-owned
+  // copy streams; in_free / out_free mark when the context stream has consumed / the output
+  // copy stream has drained the staging vector
+  void* stage_in = nullptr;
+  void* stage_out = nullptr;
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t ev_in_ready = nullptr, ev_in_free = nullptr, ev_out_ready = nullptr, ev_out_free = nullptr;
+  bool stage_pending = false;  // a staged vector waits for aqc_set_initial_state(AQC_INIT_STAGED)
+
   bool have_state = false;
   bool hist_ready = false;
   int64_t step = 0, nsteps = 0, evals = 0;
@@ -997,6 +1006,26 @@ namespace aqc {
 void set_global_error(const char* msg) { g_create_error = msg; }
 }  // namespace aqc
 
+namespace {
+
+// Wait for and destroy the copy streams and events of the staged transfers.
+void release_transfers(aqc_ctx* c) {
+  if (c->copy_in) cudaStreamSynchronize(c->copy_in);
+  if (c->copy_out) cudaStreamSynchronize(c->copy_out);
+  cudaEvent_t* evs[4] = {&c->ev_in_ready, &c->ev_in_free, &c->ev_out_ready, &c->ev_out_free};
+  for (cudaEvent_t* e : evs) {
+    if (*e) cudaEventDestroy(*e);
+    *e = nullptr;
+  }
+  if (c->copy_in) cudaStreamDestroy(c->copy_in);
+  if (c->copy_out) cudaStreamDestroy(c->copy_out);
+  c->copy_in = c->copy_out = nullptr;
+  c->stage_in = c->stage_out = nullptr;
+  c->stage_pending = false;
+}
+
+}  // namespace
+
 extern "C" {
 
 size_t aqc_workspace_bytes(int n_qubits, int precision) {
@@ -1073,6 +1102,10 @@ int aqc_create(aqc_ctx** out, int device, int precision, int n_qubits, void* wor
 
 void aqc_destroy(aqc_ctx* ctx) {
   if (!ctx) return;
+  {
+    DeviceGuard dg(ctx->device);
+    release_transfers(ctx);
+  }
   delete ctx->h_tab;
   delete ctx;
 }
@@ -1234,6 +1267,18 @@ int aqc_set_initial_state(aqc_ctx* ctx, int kind, uint64_t basis, const void* us
         if (rc) return rc;
       }
       break;
+    case AQC_INIT_STAGED:
+      if (!ctx->stage_pending) FAIL(ctx, AQC_E_STATE, "no staged initial state (aqc_stage_initial_state)");
+      CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_in_ready, 0));
+      if (ctx->permuted) {
+        int rc = to_library_order(ctx, y, ctx->stage_in);
+        if (rc) return rc;
+      } else {
+        CUDA_TRY(ctx, cudaMemcpyAsync(y, ctx->stage_in, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+      CUDA_TRY(ctx, cudaEventRecord(ctx->ev_in_free, ctx->stream));
+      ctx->stage_pending = false;
+      break;
     case AQC_INIT_USER_DEVICE:
       if (!user) FAIL(ctx, AQC_E_INVAL, "user vector is NULL");
       if (ctx->permuted) {
@@ -1344,6 +1389,75 @@ int aqc_get_state(aqc_ctx* ctx, void* dst, int dst_on_device) {
     CUDA_TRY(ctx, cudaMemcpyAsync(dst, src, (size_t)ctx->N * ctx->amp,
                                   dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return AQC_OK;
+}
+
+int aqc_transfer_attach(aqc_ctx* ctx, void* stage_in, void* stage_out) {
+  if (!ctx) return AQC_E_INVAL;
+  if (!stage_in || !stage_out) FAIL(ctx, AQC_E_INVAL, "staging vector is NULL");
+  if ((((uintptr_t)stage_in) | ((uintptr_t)stage_out)) & 255u) FAIL(ctx, AQC_E_INVAL, "staging vectors must be 256-byte aligned");
+  const size_t bytes = (size_t)ctx->N * ctx->amp;
+  const char *a = (const char*)stage_in, *b = (const char*)stage_out;
+  if (a < b + bytes && b < a + bytes) FAIL(ctx, AQC_E_INVAL, "staging vectors overlap");
+  const char *w0 = ctx->ws, *w1 = ctx->ws + ctx->wp.total;
+  if ((a < w1 && w0 < a + bytes) || (b < w1 && w0 < b + bytes)) FAIL(ctx, AQC_E_INVAL, "staging vector overlaps the workspace");
+  DeviceGuard dg(ctx->device);
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // nothing of the context still reads the old vectors
+  release_transfers(ctx);
+  cudaError_t e = cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking);
+  cudaEvent_t* evs[4] = {&ctx->ev_in_ready, &ctx->ev_in_free, &ctx->ev_out_ready, &ctx->ev_out_free};
+  for (cudaEvent_t* ev : evs)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    release_transfers(ctx);
+    FAIL(ctx, AQC_E_CUDA, "copy stream / event creation: %s", cudaGetErrorString(e));
+  }
+  // never-recorded events count as complete: the first stage and fetch wait for nothing
+  ctx->stage_in = stage_in;
+  ctx->stage_out = stage_out;
+  return AQC_OK;
+}
+
+int aqc_stage_initial_state(aqc_ctx* ctx, const void* host_src) {
+  if (!ctx) return AQC_E_INVAL;
+  if (!host_src) FAIL(ctx, AQC_E_INVAL, "host_src is NULL");
+  if (!ctx->stage_in) FAIL(ctx, AQC_E_STATE, "no staging vectors (aqc_transfer_attach)");
+  DeviceGuard dg(ctx->device);
+  CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->copy_in, ctx->ev_in_free, 0));
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->stage_in, host_src, (size_t)ctx->N * ctx->amp, cudaMemcpyHostToDevice,
+                                ctx->copy_in));
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev_in_ready, ctx->copy_in));
+  ctx->stage_pending = true;
+  return AQC_OK;
+}
+
+int aqc_fetch_state(aqc_ctx* ctx, void* host_dst) {
+  if (!ctx) return AQC_E_INVAL;
+  if (!host_dst) FAIL(ctx, AQC_E_INVAL, "host_dst is NULL");
+  if (!ctx->stage_out) FAIL(ctx, AQC_E_STATE, "no staging vectors (aqc_transfer_attach)");
+  DeviceGuard dg(ctx->device);
+  const size_t bytes = (size_t)ctx->N * ctx->amp;
+  CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_out_free, 0));
+  if (ctx->permuted) {
+    int rc = to_qubit_order(ctx, ctx->stage_out, ctx->vec[V_Y]);
+    if (rc) return rc;
+  } else {
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->stage_out, ctx->vec[V_Y], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev_out_ready, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->copy_out, ctx->ev_out_ready, 0));
+  CUDA_TRY(ctx, cudaMemcpyAsync(host_dst, ctx->stage_out, bytes, cudaMemcpyDeviceToHost, ctx->copy_out));
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev_out_free, ctx->copy_out));
+  return AQC_OK;
+}
+
+int aqc_transfer_wait(aqc_ctx* ctx) {
+  if (!ctx) return AQC_E_INVAL;
+  if (!ctx->stage_in) return AQC_OK;
+  DeviceGuard dg(ctx->device);
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->copy_in));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->copy_out));
   return AQC_OK;
 }
 

@@ -46,9 +46,10 @@ class Context:
     def close(self):
         if getattr(self, "handle", None):
             self.stream.synchronize()  # this context's work only, not the whole device
-            N.aqc_destroy(self.handle)
+            N.aqc_destroy(self.handle)  # waits for the staged copies
             self.handle = None
             self.workspace = None
+            self._stage = None
 
     def __del__(self):
         try:
@@ -103,9 +104,12 @@ class Context:
         N.aqc_set_integrator(self.handle, n_steps, kappa)
 
     def set_initial_state(self, state="uniform"):
-        """"uniform" (|S>), a basis index, ("dicke", k) (Eq. initstate), or a host/device vector."""
+        """"uniform" (|S>), a basis index, ("dicke", k) (Eq. initstate), "staged" (the vector of
+        the last stage_initial_state), or a host/device vector."""
         if isinstance(state, str) and state == "uniform":
             N.aqc_set_initial_state(self.handle, N.AQC_INIT_UNIFORM, 0, 0)
+        elif isinstance(state, str) and state == "staged":
+            N.aqc_set_initial_state(self.handle, N.AQC_INIT_STAGED, 0, 0)
         elif isinstance(state, tuple) and len(state) == 2 and state[0] == "dicke":
             N.aqc_set_initial_state(self.handle, N.AQC_INIT_DICKE, int(state[1]), 0)
         elif isinstance(state, (int, np.integer)):
@@ -128,6 +132,34 @@ class Context:
                 raise ValueError("state has the wrong length")
             N.aqc_set_initial_state(self.handle, N.AQC_INIT_USER_HOST, 0, a.ctypes.data)
             self.stream.synchronize()
+
+    # ---- staged host transfers (copy engines overlap the integrator)
+    def attach_transfers(self):
+        """Allocate the two device staging vectors and attach them (aqc_transfer_attach)."""
+        dt = _torch_dtype(self.precision)
+        with torch.cuda.device(self.dev):
+            self._stage = (torch.empty(self.N, dtype=dt, device=self.dev), torch.empty(self.N, dtype=dt, device=self.dev))
+        N.aqc_transfer_attach(self.handle, self._stage[0].data_ptr(), self._stage[1].data_ptr())
+
+    def stage_initial_state(self, host_tensor):
+        """Enqueue the copy of a pinned host vector (qubit order) for the next
+        set_initial_state("staged"); returns at once."""
+        if host_tensor.device.type != "cpu" or host_tensor.dtype != _torch_dtype(self.precision):
+            raise ValueError("a host tensor of the state dtype is required")
+        if host_tensor.numel() != self.N or not host_tensor.is_contiguous():
+            raise ValueError("state has the wrong length or is not contiguous")
+        N.aqc_stage_initial_state(self.handle, host_tensor.data_ptr())
+
+    def fetch_state(self, host_tensor):
+        """Enqueue the copy of psi into a pinned host tensor; valid after transfer_wait()."""
+        if host_tensor.device.type != "cpu" or host_tensor.dtype != _torch_dtype(self.precision):
+            raise ValueError("a host tensor of the state dtype is required")
+        if host_tensor.numel() != self.N or not host_tensor.is_contiguous():
+            raise ValueError("state has the wrong length or is not contiguous")
+        N.aqc_fetch_state(self.handle, host_tensor.data_ptr())
+
+    def transfer_wait(self):
+        N.aqc_transfer_wait(self.handle)
 
     def propagate(self, max_steps=-1, stats=True):
         return N.aqc_propagate(self.handle, max_steps, stats)

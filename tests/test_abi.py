@@ -47,6 +47,15 @@ def test_create_rejects_bad_arguments(native):
     assert native.aqc_version().startswith("aqc-gb300")
 
 
+def test_staged_transfer_entry_points_reject_null_context(native):
+    L = native.lib()
+    assert L.aqc_transfer_attach(None, None, None) == native.AQC_E_INVAL
+    assert L.aqc_stage_initial_state(None, None) == native.AQC_E_INVAL
+    assert L.aqc_fetch_state(None, None) == native.AQC_E_INVAL
+    assert L.aqc_transfer_wait(None) == native.AQC_E_INVAL
+    assert native.AQC_INIT_STAGED == 5
+
+
 def test_product_path_has_no_oracle_dependency():
     """The package never imports the oracle (test infrastructure only)."""
     root = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1311_3938_gb300")
