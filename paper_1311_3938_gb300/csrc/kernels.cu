@@ -637,12 +637,15 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
       }
     };
 
-    // 2. X strings with real coefficients
+    // 2. X strings with real coefficients.  In FP64 (bound by the FP64 pipe) the accumulators
+    //    start from the partial sum of the earlier layouts, one add per component fewer; in FP32
+    //    (bound by HBM) the partial sum is added last
+    constexpr bool kFp64 = sizeof(R) == 8;
     R ar[G], ai[G];
 #pragma unroll
     for (int g = 0; g < G; g++) {
-      ar[g] = (R)0;
-      ai[g] = (R)0;
+      ar[g] = kFp64 ? qv[g].x : (R)0;
+      ai[g] = kFp64 ? qv[g].y : (R)0;
     }
     // products flipping no register-held bit: one 16-byte shared load per half, no selects
     if (full) {
@@ -738,8 +741,10 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
         ar[g] += d * own[g].x;
         ai[g] += d * own[g].y;
       }
-      ar[g] += qv[g].x;
-      ai[g] += qv[g].y;
+      if (!kFp64) {
+        ar[g] += qv[g].x;
+        ai[g] += qv[g].y;
+      }
     }
     // HINT 2: the partial sum is dead after this read; drop its L2 lines instead of writing
     // them back (one lane per 128-byte line: eight lanes of 16 bytes)
@@ -749,7 +754,11 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
     }
     // 5. epilogue
     const R h = T.h;
+    // corrector and predictor weights h/24 * (9, 19, -5, 1) and h/24 * (55, -59, 37, -9); in
+    // FP64 applied as chains of fused multiply-adds (fewer FP64 instructions)
     const R h24 = h / (R)24;
+    const R c9 = (R)9 * h24, c19 = (R)19 * h24, c5 = (R)5 * h24;
+    const R p55 = (R)55 * h24, p59 = (R)59 * h24, p37 = (R)37 * h24, p9 = (R)9 * h24;
     C2 o1[G], o2[G], o3[G];
 #pragma unroll
     for (int g = 0; g < G; g++) {
@@ -766,10 +775,17 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
         // f_{n+1} = -i H p_{n+1};  corrector y_{n+1};  predictor p_{n+2}  (Sec. I.B)
         const C2 fn = C2{ai[g], -ar[g]};
         C2 yn, pn;
-        yn.x = y0[g].x + h24 * ((R)9 * fn.x + (R)19 * a[g].x - (R)5 * b[g].x + c[g].x);
-        yn.y = y0[g].y + h24 * ((R)9 * fn.y + (R)19 * a[g].y - (R)5 * b[g].y + c[g].y);
-        pn.x = yn.x + h24 * ((R)55 * fn.x - (R)59 * a[g].x + (R)37 * b[g].x - (R)9 * c[g].x);
-        pn.y = yn.y + h24 * ((R)55 * fn.y - (R)59 * a[g].y + (R)37 * b[g].y - (R)9 * c[g].y);
+        if (kFp64) {
+          yn.x = fma(c9, fn.x, fma(c19, a[g].x, fma(-c5, b[g].x, fma(h24, c[g].x, y0[g].x))));
+          yn.y = fma(c9, fn.y, fma(c19, a[g].y, fma(-c5, b[g].y, fma(h24, c[g].y, y0[g].y))));
+          pn.x = fma(p55, fn.x, fma(-p59, a[g].x, fma(p37, b[g].x, fma(-p9, c[g].x, yn.x))));
+          pn.y = fma(p55, fn.y, fma(-p59, a[g].y, fma(p37, b[g].y, fma(-p9, c[g].y, yn.y))));
+        } else {
+          yn.x = y0[g].x + h24 * ((R)9 * fn.x + (R)19 * a[g].x - (R)5 * b[g].x + c[g].x);
+          yn.y = y0[g].y + h24 * ((R)9 * fn.y + (R)19 * a[g].y - (R)5 * b[g].y + c[g].y);
+          pn.x = yn.x + h24 * ((R)55 * fn.x - (R)59 * a[g].x + (R)37 * b[g].x - (R)9 * c[g].x);
+          pn.y = yn.y + h24 * ((R)55 * fn.y - (R)59 * a[g].y + (R)37 * b[g].y - (R)9 * c[g].y);
+        }
         o1[g] = yn;
         o2[g] = fn;
         o3[g] = pn;
