@@ -368,6 +368,28 @@ def _main():
         print(json.dumps(run_batch512()), flush=True)
 
 
+def admit_ready(pending, now, used, budget, n_members, max_members, batch_max_n, start):
+    """Admit arrived jobs from the head of `pending` (sorted by arrival) in FIFO order.
+
+    A job is admitted while its workspace fits the HBM budget (`used` + its bytes <= `budget`)
+    and, for a small job (n <= batch_max_n, a batch member), while the batch has fewer than
+    `max_members` members (`n_members()`); the first arrived job that does not fit waits and
+    blocks the jobs behind it (no overtaking).  Each admitted job leaves `pending` and is passed
+    to `start(job, small)`, which creates its context.  `now()` is read for every job, so jobs
+    that arrive while earlier ones start are admitted in the same pass.  Returns the new
+    `used`."""
+    while pending and pending[0].arrival <= now():
+        job = pending[0]
+        need = job.workspace_bytes()
+        small = job.n <= batch_max_n
+        if used + need > budget or (small and n_members() >= max_members):
+            break
+        pending.pop(0)
+        used += need
+        start(job, small)
+    return used
+
+
 class Server:
     """Continuous-batching request loop (see the module docstring)."""
 
@@ -410,16 +432,9 @@ class Server:
                 break
             # admission: FIFO among arrived jobs, as memory allows
             ta = time.perf_counter()
-            while pending and pending[0].arrival <= now():
-                job = pending[0]
-                need = job.workspace_bytes()
-                small = job.n <= self.batch_max_n
-                if self.used + need > self.budget or (small and len(in_batch) >= self.max_members):
-                    break
-                pending.pop(0)
+
+            def start(job, small):
                 job.admitted = now()
-                self.used += need
-                self.peak_used = max(self.peak_used, self.used)
                 if small:
                     ctx, inst = make_context(job, self.device)
                     slot = self.batch.add(ctx)
@@ -428,6 +443,10 @@ class Server:
                     stream = torch.cuda.Stream(self.device, priority=self.lo_prio)
                     ctx, inst = make_context(job, self.device, stream=stream)
                     big.append([job, ctx, inst, stream, None, 0, []])
+
+            self.used = admit_ready(pending, now, self.used, self.budget, lambda: len(in_batch), self.max_members,
+                                    self.batch_max_n, start)
+            self.peak_used = max(self.peak_used, self.used)
             prof["admit_s"] += time.perf_counter() - ta
             self.occupancy.append(self.used / max(1, self.budget))
             if not in_batch and not big:
