@@ -1,6 +1,8 @@
 """Planted mistakes in the oracle (on the CPU): each plausible error — a wrong sign, a dropped
 term, a wrong coefficient, a wrong stage time, a transposed index — is written into a temporary
 copy of the C oracle, and at least one pin of tests/test_oracle_pins.py must fail with it.
+The clause-by-clause coefficients of Eq. kpath get three: the two segment weights swapped, the
+partial sum H_k missing its own clause, and the two segments meeting at s = k/m both counted.
 This shows the pins are sharp enough to catch mistakes anywhere in the oracle."""
 import ctypes as C
 import os
@@ -8,6 +10,7 @@ import subprocess
 
 import pytest
 
+import test_oracle_cbc_pins as cbc
 import test_oracle_pins as pins
 from oracle import oracle as O
 
@@ -24,6 +27,16 @@ MUTATIONS = {
     "predictor_dropped_term": ("+ 37.0 * fn2[i] - 9.0 * fn3[i]);", "+ 37.0 * fn2[i]);"),
     "corrector_coefficient": ("+ 19.0 * fn[i] - 5.0 * fn1[i]", "+ 18.0 * fn[i] - 5.0 * fn1[i]"),
     "smoothstep": ("s = 3.0 * tau * tau - 2.0 * tau * tau * tau;", "s = 3.0 * tau * tau - 2.0 * tau * tau;"),
+    # clause-by-clause coefficients of Eq. kpath
+    "kpath_weights_swapped": ("return (1.0 - sk) * (double)in_prev + sk * (double)in_cur;",
+                              "return sk * (double)in_prev + (1.0 - sk) * (double)in_cur;"),
+    "kpath_partial_sum_index": ("int in_cur = (k <= m - 1) && (j <= k);", "int in_cur = (k <= m - 1) && (j < k);"),
+    "kpath_segments_summed": (
+        "    if (!(sk >= 0.0 && sk < 1.0)) continue;",
+        "    if (!(sk >= 0.0 && sk <= 1.0)) continue;\n"
+        "    if (sk == 1.0 && k < m) { double sn = sk - 1.0; int pn = (j <= k); int cn = (k + 1 <= m - 1) && (j <= k + 1);\n"
+        "      return (1.0 - sk) * (double)((k - 1 >= 1) && (j <= k - 1)) + sk * (double)((k <= m - 1) && (j <= k))\n"
+        "             + (1.0 - sn) * (double)pn + sn * (double)cn; }"),
 }
 
 PINS = [
@@ -37,6 +50,8 @@ PINS = [
     lambda: pins.test_product_state_time_dependent(1),
     pins.test_x_driver_ground_state_and_spectrum,
     pins.test_c_schedule_weights_closed_form,
+    lambda: cbc.test_segments_interpolate_partial_sums(1),
+    lambda: cbc.test_one_segment_on_step_grids(7, 2940),
 ]
 
 
