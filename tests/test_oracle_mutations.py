@@ -102,3 +102,51 @@ def test_planted_mistake_is_caught(tmp_path, monkeypatch, name):
         except RuntimeError:
             failed.append(i)
     assert failed, f"no pin caught the planted mistake {name}"
+
+
+# Planted mistakes in the oracle's Python builders of the XY / XYZ algorithms (Sec. III.A.2-3):
+# the function's own source with one substitution, run in the oracle module's namespace.
+PY_MUTATIONS = {
+    "xy_yy_sign": ("add_xy_driver", "H.add_term(group, m, m, -omega * v / 2.0)",
+                   "H.add_term(group, m, m, omega * v / 2.0)"),
+    "xy_identity_prefactor": ("add_xy_driver", "3.0 * len(clauses) * omega", "2.0 * len(clauses) * omega"),
+    "xyz_zz_dropped": ("add_xyz_driver", "H.add_term(group, 0, m, -a)  # Z_i Z_j", "pass"),
+    "xyz_pair_weight": ("add_xyz_driver", "a = omega * v / 2.0", "a = omega * v"),
+    "pair_counts_with_self_pairs": ("clause_pair_counts", "for y in range(x + 1, 3):", "for y in range(x, 3):"),
+    "dicke_normalisation": ("dicke_state", "1.0 / math.sqrt(math.comb(n, k))", "1.0 / math.comb(n, k)"),
+}
+
+
+def _xy_pins():
+    import test_oracle_xy_pins as xy
+
+    return [
+        lambda: xy.test_drivers_on_basis_states(1),
+        xy.test_dicke_states_are_xyz_ground_states,
+        lambda: xy.test_paths_conserve_hamming_weight("xy"),
+    ]
+
+
+def test_unmutated_xy_builders_pass_their_pins():
+    for p in _xy_pins():
+        p()
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTATIONS))
+def test_planted_mistake_in_xy_builders_is_caught(monkeypatch, name):
+    import inspect
+    import textwrap
+
+    func, old, new = PY_MUTATIONS[name]
+    src = textwrap.dedent(inspect.getsource(getattr(O, func)))
+    assert src.count(old) == 1, name
+    ns = dict(vars(O))
+    exec(compile(src.replace(old, new), O.__file__, "exec"), ns)
+    monkeypatch.setattr(O, func, ns[func])
+    failed = []
+    for i, p in enumerate(_xy_pins()):
+        try:
+            p()
+        except (AssertionError, RuntimeError, ValueError):
+            failed.append(i)
+    assert failed, f"no pin caught the planted mistake {name}"
