@@ -319,8 +319,9 @@ int aqc_tridiag_eigvals(int k, const double *a, const double *b, int n_eig, doub
  * on `cuda_stream`, and synchronises that stream.  The first call on a device looks up the
  * scratch address once; make that first call before any stream capture.  All calls on a
  * device share the scratch, so calls that overlap on the GPU (different streams or threads
- * without ordering) race and give wrong results.  n_amplitudes must be in [1, 2^31]; larger
- * sizes are rejected with AQC_E_INVAL; errors are described by aqc_last_error(NULL). */
+ * without ordering) race and give wrong results.  n_amplitudes must be in [1, 2^31] and psi
+ * aligned to its amplitude size (16 bytes for AQC_C128, 8 for AQC_C64); other sizes and
+ * pointers are rejected with AQC_E_INVAL; errors are described by aqc_last_error(NULL). */
 int aqc_norm2_noalloc(int precision, const void *psi, uint64_t n_amplitudes, void *cuda_stream, double *out);
 
 /* Total kernel launches the context has issued since creation (monotone counter). */

@@ -41,6 +41,10 @@ extern "C" int aqc_norm2_noalloc(int precision, const void* psi, uint64_t n_ampl
     set_global_error("aqc_norm2_noalloc: psi and out must not be NULL");
     return AQC_E_INVAL;
   }
+  if (((uintptr_t)psi) & (precision == AQC_C128 ? 15u : 7u)) {
+    set_global_error("aqc_norm2_noalloc: psi must be aligned to its amplitude size (16 or 8 bytes)");
+    return AQC_E_INVAL;
+  }
   if (n_amplitudes == 0 || n_amplitudes > (1ull << kMaxN)) {
     set_global_error("aqc_norm2_noalloc: n_amplitudes must be in [1, 2^31]");
     return AQC_E_INVAL;

@@ -56,6 +56,17 @@ def test_staged_transfer_entry_points_reject_null_context(native):
     assert native.AQC_INIT_STAGED == 5
 
 
+def test_norm2_noalloc_rejects_misaligned_vectors(native):
+    """Checked on the host before any device call: the pointer is never dereferenced."""
+    L = native.lib()
+    L.aqc_norm2_noalloc.restype = C.c_int
+    L.aqc_norm2_noalloc.argtypes = [C.c_int, C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(C.c_double)]
+    out = C.c_double()
+    assert L.aqc_norm2_noalloc(native.AQC_C128, 0x10008, 4, None, C.byref(out)) == native.AQC_E_INVAL
+    assert b"aligned" in L.aqc_last_error(None)
+    assert L.aqc_norm2_noalloc(native.AQC_C64, 0x10004, 4, None, C.byref(out)) == native.AQC_E_INVAL
+
+
 def test_product_path_has_no_oracle_dependency():
     """The package never imports the oracle (test infrastructure only)."""
     root = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1311_3938_gb300")

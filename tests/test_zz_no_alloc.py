@@ -62,3 +62,19 @@ def test_norm2_noalloc_rejects_bad_sizes(lib):
     assert lib.aqc_norm2_noalloc(1, psi.data_ptr(), (1 << 31) + 1, None, C.byref(out)) == -1
     assert b"n_amplitudes" in lib.aqc_last_error(None)
     assert lib.aqc_norm2_noalloc(7, psi.data_ptr(), 4, None, C.byref(out)) == -1
+
+
+@pytest.mark.parametrize("count,offset", [(1, 0), (3, 0), ((1 << 20) + 1, 0), (5, 1), ((1 << 16) + 3, 1)])
+def test_norm2_noalloc_odd_lengths_and_offsets(lib, count, offset):
+    """complex64 in FP64 against numpy: an odd length takes its last amplitude apart from the
+    16-byte loads; a vector 8 bytes off a 16-byte boundary takes one 8-byte load per amplitude."""
+    rng = np.random.default_rng(count)
+    v = (rng.standard_normal(count + 1) + 1j * rng.standard_normal(count + 1)).astype(np.complex64)
+    buf = torch.from_numpy(v).cuda()  # one spare amplitude: the offset view stays inside
+    assert buf.data_ptr() % 256 == 0
+    ref = float(np.sum(np.abs(v[offset:offset + count].astype(np.complex128)) ** 2))
+    out = C.c_double(-1.0)
+    rc = lib.aqc_norm2_noalloc(1, buf.data_ptr() + 8 * offset, count, torch.cuda.current_stream().cuda_stream,
+                               C.byref(out))
+    assert rc == 0, lib.aqc_last_error(None)
+    assert abs(out.value - ref) <= 1e-6 * ref, (out.value, ref)
