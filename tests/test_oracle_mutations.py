@@ -50,6 +50,7 @@ PINS = [
     lambda: pins.test_product_state_time_dependent(1),
     pins.test_x_driver_ground_state_and_spectrum,
     pins.test_c_schedule_weights_closed_form,
+    lambda: pins.test_diagonal_hamiltonian_phases(1),
     lambda: cbc.test_segments_interpolate_partial_sums(1),
     lambda: cbc.test_one_segment_on_step_grids(7, 2940),
 ]

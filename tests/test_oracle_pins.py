@@ -390,3 +390,25 @@ def test_smoothstep_schedule_weights():
     for t, s in [(0.0, 0.0), (5.0, 0.5), (10.0, 1.0), (2.5, 3 * 0.0625 - 2 * 0.015625)]:
         w = sc.weights(t)
         assert abs(w[0] - (1 - s)) < 1e-15 and abs(w[1] - s) < 1e-15
+
+
+@pytest.mark.parametrize("s_kind", [0, 1])
+def test_diagonal_hamiltonian_phases(s_kind):
+    """A diagonal H(t) = A(s) c 1 + B(s) H_f (clause penalties, no driver) turns each amplitude
+    by exp(-i (c int A dt + d_z int B dt)); int A dt = int B dt = T/2 for both s(t) (the
+    smoothstep is symmetric about t = T/2).  The oracle reaches that closed form at 4th order."""
+    inst = generate_ec3(6, 5)
+    n, T, c = inst.n, 4.0, 1.5
+    H = O.Hamiltonian(n)
+    O.add_ec3_clauses(H, inst.clauses, 1)
+    H.add_term(0, 0, 0, c)
+    d = np.zeros(1 << n)
+    for z in range(1 << n):  # penalty [k != 1] counted by hand over the clauses
+        d[z] = sum(1.0 for cl in inst.clauses if sum((z >> b) & 1 for b in cl) != 1)
+    psi0 = random_state(n, 3)
+    exact = psi0 * np.exp(-1j * (c * T / 2 + d * T / 2))
+    sched = O.linear_path(T, s_kind)
+    N = O.step_count(H, sched)
+    errs = [np.linalg.norm(O.propagate(H, sched, k * N, psi0).psi - exact) for k in (1, 2)]  # unit-norm psi0
+    assert errs[0] < 5e-5
+    assert 10.0 < errs[0] / errs[1] < 24.0  # 4th order: halving h divides the error by ~16
