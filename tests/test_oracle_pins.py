@@ -412,3 +412,27 @@ def test_diagonal_hamiltonian_phases(s_kind):
     errs = [np.linalg.norm(O.propagate(H, sched, k * N, psi0).psi - exact) for k in (1, 2)]  # unit-norm psi0
     assert errs[0] < 5e-5
     assert 10.0 < errs[0] / errs[1] < 24.0  # 4th order: halving h divides the error by ~16
+
+
+def test_interacting_path_matches_library_ode_solver():
+    """EC3 n = 6 with the X driver and XX couplings on the nonlinear path (all three groups time
+    dependent): the oracle's PEC solution against scipy's DOP853 (an 8th-order Runge-Kutta
+    method, tight tolerances) on the dense H(t), at the step rule's h and at h/2 (4th order)."""
+    from scipy.integrate import solve_ivp
+
+    inst = generate_ec3(6, 2)
+    H = O.ec3_hamiltonian(inst, pairs=xx_pairs(6, 2))
+    T = 3.0
+    sched = O.nonlinear_path(T)
+    M = [O.dense_matrix(H, [1.0 * (g == k) for k in range(3)] + [0.0]) for g in range(3)]
+
+    def rhs(t, y):
+        w = sched.weights(t)
+        return -1j * ((w[0] * M[0] + w[1] * M[1] + w[2] * M[2]) @ y)
+
+    psi0 = O.uniform_state(6)
+    ref = solve_ivp(rhs, (0.0, T), psi0, method="DOP853", rtol=1e-12, atol=1e-14).y[:, -1]
+    N = O.step_count(H, sched)
+    errs = [np.linalg.norm(O.propagate(H, sched, k * N, psi0).psi - ref) for k in (1, 2)]
+    assert errs[0] < 1e-6
+    assert 10.0 < errs[0] / errs[1] < 24.0
