@@ -104,3 +104,29 @@ def test_xyz_algorithm_adiabatic_limit():
         assert E >= (1.0 - p1) - 1e-9  # Sec. II.B: every excited state costs at least Omega
         P1.append(p1)
     assert P1[1] > 0.9 and P1[1] > P1[0]
+
+
+def test_xy_catalyst_path_matches_library_ode_solver():
+    """The XY algorithm with the catalyst (Eq. nlpath, alpha = 8) from the Dicke state: the
+    oracle's PEC solution against scipy's DOP853 on the dense H(t) (Y products make it
+    complex), at the step rule's h and at h/2 (4th order)."""
+    from scipy.integrate import solve_ivp
+
+    inst = generate_ec3(6, 3)
+    n = inst.n
+    k = bin(inst.solution).count("1")
+    H = O.xy_hamiltonian(inst, driver="xy", catalyst=list(inst.clauses[:-1]))
+    T = 2.0
+    sched = O.nonlinear_path(T, alpha=8.0)
+    M = [O.dense_matrix(H, [1.0 * (g == j) for j in range(3)] + [0.0]) for g in range(3)]
+
+    def rhs(t, y):
+        w = sched.weights(t)
+        return -1j * ((w[0] * M[0] + w[1] * M[1] + w[2] * M[2]) @ y)
+
+    psi0 = O.dicke_state(n, k)
+    ref = solve_ivp(rhs, (0.0, T), psi0, method="DOP853", rtol=1e-12, atol=1e-14).y[:, -1]
+    N = O.step_count(H, sched)
+    errs = [np.linalg.norm(O.propagate(H, sched, j * N, psi0).psi - ref) for j in (1, 2)]
+    assert errs[0] < 2e-6
+    assert 10.0 < errs[0] / errs[1] < 24.0
