@@ -95,3 +95,30 @@ def test_one_segment_on_step_grids(m, N):
             if 0.0 <= s < 1.0:
                 ref = (1 - sk) * (k - 1 if 1 <= k - 1 <= m - 1 else 0) + sk * (k if k <= m - 1 else 0)
             assert abs(d - ref) < 1e-9, (n, s * m, d, ref)
+
+
+def test_cbc_path_matches_library_ode_solver():
+    """The clause-by-clause XY path from the Dicke state against scipy's DOP853 on the dense
+    H(t) of the segment formula, integrated segment by segment so that the library solver never
+    steps across a kink at s = k/m.  The fixed-step PEC history spans the kinks, where dH/dt
+    jumps, so its error falls at 2nd order rather than 4th."""
+    from scipy.integrate import solve_ivp
+
+    inst = generate_ec3(6, 3)
+    n, cl = inst.n, list(inst.clauses)
+    m = len(cl)
+    H = O.xy_hamiltonian(inst, driver="xy")
+    O.add_clause_by_clause(H, cl, group=2)
+    T = 2.0
+    sched = O.clause_by_clause_path(T)
+    psi0 = O.dicke_state(n, bin(inst.solution).count("1"))
+    y, t0 = psi0.copy(), 0.0
+    for j in range(1, m + 1):
+        t1 = T * j / m
+        sol = solve_ivp(lambda t, v: -1j * (O.dense_matrix(H, sched.weights(t)) @ v), (t0, t1), y,
+                        method="DOP853", rtol=1e-12, atol=1e-14)
+        y, t0 = sol.y[:, -1], t1
+    N = O.step_count(H, sched)
+    errs = [np.linalg.norm(O.propagate(H, sched, j * N, psi0).psi - y) for j in (1, 2)]
+    assert errs[0] < 1e-5
+    assert 3.0 < errs[0] / errs[1] < 6.0
