@@ -94,7 +94,9 @@ size_t aqc_workspace_bytes(int n_qubits, int precision);
 int aqc_create(aqc_ctx **out, int device, int precision, int n_qubits, void *workspace, size_t workspace_bytes,
                void *cuda_stream);
 
-/* Release the host-side context (the workspace stays the caller's). NULL is ignored. */
+/* Release the host-side context (the workspace and staging vectors stay the caller's); waits
+ * for pending staged copies and destroys the copy streams of aqc_transfer_attach.  NULL is
+ * ignored. */
 void aqc_destroy(aqc_ctx *ctx);
 
 /* Order all later work of the context on `cuda_stream`. */
