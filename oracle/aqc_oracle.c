@@ -20,7 +20,9 @@
  *     predictor, Adams-Moulton-4 corrector, PEC mode, fixed step h = T/N, started with three
  *     classical Runge-Kutta-4 steps.
  * Pins: tests/test_oracle_pins.py (dense Kronecker matrices, exact exponentials, closed
- * forms, convergence order).
+ * forms, convergence order, a library ODE solver), tests/test_oracle_xy_pins.py and
+ * tests/test_oracle_cbc_pins.py; tests/test_oracle_mutations.py plants mistakes in a copy of
+ * this file and checks that a pin catches each.
  */
 #include <math.h>
 #include <pthread.h>

@@ -18,8 +18,10 @@ Contents
   * observables: P_1 = |<w|psi>|^2 and E = <psi|H_f|psi> (Sec. II.B).
   * `step_count`: the fixed-step rule h = T/N, N = ceil(T * Lambda / kappa).
 
-Every function here is pinned by tests/test_oracle_pins.py against closed forms, dense linear
-algebra or brute force; none is "parity unpinned".
+Every function here is pinned by tests/test_oracle_pins.py, tests/test_oracle_xy_pins.py and
+tests/test_oracle_cbc_pins.py against closed forms, dense linear algebra, brute force or a
+library ODE solver; none is "parity unpinned".  tests/test_oracle_mutations.py plants mistakes
+in the builders of the XY/XYZ algorithms and checks that a pin catches each.
 """
 from __future__ import annotations
 
