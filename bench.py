@@ -472,7 +472,8 @@ def run_ours(a):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "c64 (f32 arithmetic, f64 reductions)",
+        "dtype": "f32",
+        "precision": "complex64 state, FP32 arithmetic, FP64 reductions",
         "data": "synthetic (seeded EC3 instance)",
         "config": {
             "workload": f"ec3-n{n}-seed{SEED}-linear-T{T_RUN:g}-uniform",
@@ -518,6 +519,7 @@ def run_ours(a):
     if r128 is not None:
         flops = pec_flops_c128(n) * (1 << n)
         line["c128"] = {
+            "dtype": "f64",
             "value": r128["value"],
             "unit": "GB/s",
             "ms_per_step": r128["ms_per_step"],
