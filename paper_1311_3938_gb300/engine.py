@@ -135,11 +135,13 @@ class Context:
 
     # ---- staged host transfers (copy engines overlap the integrator)
     def attach_transfers(self):
-        """Allocate the two device staging vectors and attach them (aqc_transfer_attach)."""
+        """Allocate the two device staging vectors and attach them (aqc_transfer_attach).  Called
+        again, it keeps the previous vectors alive until the library has finished their copies."""
         dt = _torch_dtype(self.precision)
         with torch.cuda.device(self.dev):
-            self._stage = (torch.empty(self.N, dtype=dt, device=self.dev), torch.empty(self.N, dtype=dt, device=self.dev))
-        N.aqc_transfer_attach(self.handle, self._stage[0].data_ptr(), self._stage[1].data_ptr())
+            stage = (torch.empty(self.N, dtype=dt, device=self.dev), torch.empty(self.N, dtype=dt, device=self.dev))
+        N.aqc_transfer_attach(self.handle, stage[0].data_ptr(), stage[1].data_ptr())
+        self._stage = stage  # the previous pair (if any) is released only now
 
     def stage_initial_state(self, host_tensor):
         """Enqueue the copy of a pinned host vector (qubit order) for the next
