@@ -41,6 +41,8 @@ class Context:
         self._ws_ptr = (base + 255) // 256 * 256
         self.handle = N.aqc_create(device, precision, n, self._ws_ptr, self.ws_bytes, self.stream.cuda_stream)
         self.N = 1 << n
+        self._stage = None  # staging vectors of aqc_transfer_attach
+        self._in_flight = []
 
     # ---- lifetime
     def close(self):
@@ -50,6 +52,7 @@ class Context:
             self.handle = None
             self.workspace = None
             self._stage = None
+            self._in_flight = []
 
     def __del__(self):
         try:
@@ -142,6 +145,7 @@ class Context:
             stage = (torch.empty(self.N, dtype=dt, device=self.dev), torch.empty(self.N, dtype=dt, device=self.dev))
         N.aqc_transfer_attach(self.handle, stage[0].data_ptr(), stage[1].data_ptr())
         self._stage = stage  # the previous pair (if any) is released only now
+        self._in_flight = []  # host tensors of enqueued copies (attach waited for the earlier ones)
 
     def stage_initial_state(self, host_tensor):
         """Enqueue the copy of a pinned host vector (qubit order) for the next
@@ -151,6 +155,7 @@ class Context:
         if host_tensor.numel() != self.N or not host_tensor.is_contiguous():
             raise ValueError("state has the wrong length or is not contiguous")
         N.aqc_stage_initial_state(self.handle, host_tensor.data_ptr())
+        self._in_flight.append(host_tensor)  # alive until its copy is known to be done
 
     def fetch_state(self, host_tensor):
         """Enqueue the copy of psi into a pinned host tensor; valid after transfer_wait()."""
@@ -159,9 +164,11 @@ class Context:
         if host_tensor.numel() != self.N or not host_tensor.is_contiguous():
             raise ValueError("state has the wrong length or is not contiguous")
         N.aqc_fetch_state(self.handle, host_tensor.data_ptr())
+        self._in_flight.append(host_tensor)
 
     def transfer_wait(self):
         N.aqc_transfer_wait(self.handle)
+        self._in_flight.clear()
 
     def propagate(self, max_steps=-1, stats=True):
         return N.aqc_propagate(self.handle, max_steps, stats)
