@@ -133,13 +133,15 @@ static void *scatter_worker(void *arg) {
   for (int t = 0; t < H->nterms; t++) {
     double c = jb->w[H->term_group[t]] * H->coef[t];
     if (c != 0.0) {
+      /* the qubits the product acts on, lowest first (identity elsewhere) */
+      const uint64_t act = H->xmask[t] | H->zmask[t];
       for (uint64_t z = jb->lo; z < jb->hi; z++) {
         double re = jb->psi[2 * z], im = jb->psi[2 * z + 1];
         uint64_t zout = z;
-        for (int q = 0; q < H->n; q++) {
+        for (uint64_t rest = act; rest != 0; rest &= rest - 1) {
+          int q = __builtin_ctzll(rest);
           int xq = (int)((H->xmask[t] >> q) & 1u);
           int zq = (int)((H->zmask[t] >> q) & 1u);
-          if (!xq && !zq) continue; /* identity on this qubit */
           int b = (int)((z >> q) & 1u);
           int nb = pauli_on_bit(xq, zq, b, &re, &im);
           zout = (zout & ~(1ull << q)) | ((uint64_t)nb << q);
@@ -213,10 +215,10 @@ int or_hpsi_at(const or_ham *H, const double w[4], const double *psi, int64_t nz
       uint64_t zsrc = z ^ H->xmask[t];
       double re = psi[2 * zsrc], im = psi[2 * zsrc + 1];
       uint64_t zimg = zsrc;
-      for (int q = 0; q < H->n; q++) {
+      for (uint64_t rest = H->xmask[t] | H->zmask[t]; rest != 0; rest &= rest - 1) {
+        int q = __builtin_ctzll(rest); /* the qubits the product acts on, lowest first */
         int xq = (int)((H->xmask[t] >> q) & 1u);
         int zq = (int)((H->zmask[t] >> q) & 1u);
-        if (!xq && !zq) continue;
         int b = (int)((zsrc >> q) & 1u);
         int nb = pauli_on_bit(xq, zq, b, &re, &im);
         zimg = (zimg & ~(1ull << q)) | ((uint64_t)nb << q);
