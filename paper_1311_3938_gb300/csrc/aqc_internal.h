@@ -116,6 +116,8 @@ struct ApplyParams {
   const void* qin;   // partial sum from earlier layouts (nullable)
   void* qout;        // PARTIAL: output partial sum
   void* y;           // STEP: y_n -> y_{n+1};  RK4: y (stage 4 writes y)
+  void* yout;        // STEP: where y_{n+1} goes (nullptr: in place over y, the fixed-step grid;
+                     // a second vector under step-size control, so a rejected step keeps y_n)
   const void* f0;    // STEP: f_n
   const void* f1;    // STEP: f_{n-1}
   const void* f2;    // STEP: f_{n-2}

@@ -227,13 +227,17 @@ struct TileCtx {
   uint32_t tsize, tmask;
   int np, npf, nh, ngl, ng, nz, ncls, tcls, stage;
   R dconst, wtab, h;
+  // h/24 of the PEC corrector and predictor as a sum hi + lo of two state-precision numbers
+  // (lo = 0 in FP64): every PEC step scales its increment by h/24, so a step size rounded once
+  // to FP32 would be a time-scale error of up to 2^-24 that accumulates over the whole run
+  R h24, h24lo;
   int step_k;          // clause-by-clause segment (0: none active)
   R step_wdone, step_wact;
   const DevTables* tab;
   const uint8_t* dcode;
   double w0, w1, w2;
   const C2 *src, *qin, *f0, *f1, *f2;
-  C2 *qout, *y, *fout, *pout, *acc;
+  C2 *qout, *y, *yout, *fout, *pout, *acc;
   C2* s_p;
   uint8_t* s_code;
   PFlip<R>* s_pf;
@@ -242,6 +246,14 @@ struct TileCtx {
   double* s_red;
   uint64_t pol_keep, pol_drop;  // L2 policies (evict_last / evict_first) of hinted tile passes
 };
+
+// h/24 split into the state precision: hi = h/24 rounded, lo = the rounding residual (FP32 only)
+template <typename R>
+__device__ __forceinline__ void set_h24(TileCtx<R>& T, double h) {
+  const double e = h / 24.0;
+  T.h24 = (R)e;
+  T.h24lo = sizeof(R) == 8 ? (R)0 : (R)(e - (double)T.h24);
+}
 
 __device__ __forceinline__ double pick3(double a, double b, double c, int g) { return g == 0 ? a : (g == 1 ? b : c); }
 
@@ -756,7 +768,8 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
     const R h = T.h;
     // corrector and predictor weights h/24 * (9, 19, -5, 1) and h/24 * (55, -59, 37, -9); in
     // FP64 applied as chains of fused multiply-adds (fewer FP64 instructions)
-    const R h24 = h / (R)24;
+    const R h24 = kFp64 ? h / (R)24 : T.h24;
+    const R h24lo = T.h24lo;
     const R c9 = (R)9 * h24, c19 = (R)19 * h24, c5 = (R)5 * h24;
     const R p55 = (R)55 * h24, p59 = (R)59 * h24, p37 = (R)37 * h24, p9 = (R)9 * h24;
     C2 o1[G], o2[G], o3[G];
@@ -781,10 +794,15 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
           pn.x = fma(p55, fn.x, fma(-p59, a[g].x, fma(p37, b[g].x, fma(-p9, c[g].x, yn.x))));
           pn.y = fma(p55, fn.y, fma(-p59, a[g].y, fma(p37, b[g].y, fma(-p9, c[g].y, yn.y))));
         } else {
-          yn.x = y0[g].x + h24 * ((R)9 * fn.x + (R)19 * a[g].x - (R)5 * b[g].x + c[g].x);
-          yn.y = y0[g].y + h24 * ((R)9 * fn.y + (R)19 * a[g].y - (R)5 * b[g].y + c[g].y);
-          pn.x = yn.x + h24 * ((R)55 * fn.x - (R)59 * a[g].x + (R)37 * b[g].x - (R)9 * c[g].x);
-          pn.y = yn.y + h24 * ((R)55 * fn.y - (R)59 * a[g].y + (R)37 * b[g].y - (R)9 * c[g].y);
+          // the weighted sums times (hi + lo): h24 * S + h24lo * S with one rounding of the sum
+          const R scx = (R)9 * fn.x + (R)19 * a[g].x - (R)5 * b[g].x + c[g].x;
+          const R scy = (R)9 * fn.y + (R)19 * a[g].y - (R)5 * b[g].y + c[g].y;
+          yn.x = y0[g].x + fma(h24, scx, h24lo * scx);
+          yn.y = y0[g].y + fma(h24, scy, h24lo * scy);
+          const R spx = (R)55 * fn.x - (R)59 * a[g].x + (R)37 * b[g].x - (R)9 * c[g].x;
+          const R spy = (R)55 * fn.y - (R)59 * a[g].y + (R)37 * b[g].y - (R)9 * c[g].y;
+          pn.x = yn.x + fma(h24, spx, h24lo * spx);
+          pn.y = yn.y + fma(h24, spy, h24lo * spy);
         }
         o1[g] = yn;
         o2[g] = fn;
@@ -819,7 +837,7 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
     }
     // stores
     if (MODE == MODE_ENERGY) continue;
-    C2* d1 = MODE == MODE_PARTIAL ? T.qout : (MODE == MODE_DERIV ? T.fout : (MODE == MODE_STEP ? T.y : nullptr));
+    C2* d1 = MODE == MODE_PARTIAL ? T.qout : (MODE == MODE_DERIV ? T.fout : (MODE == MODE_STEP ? T.yout : nullptr));
     C2* d2 = MODE == MODE_STEP ? T.fout : nullptr;
     C2* d3 = MODE == MODE_STEP ? T.pout : nullptr;
     if (MODE == MODE_RK4) {
@@ -857,6 +875,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_PARTIAL && sizeof(R) =
                        P.w[2], smem);
   T.stage = P.stage;
   T.h = (R)P.h;
+  set_h24(T, P.h);
   T.step_k = P.step_k;
   T.step_wdone = (R)P.step_wdone;
   T.step_wact = (R)P.step_wact;
@@ -864,6 +883,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_PARTIAL && sizeof(R) =
   T.qin = reinterpret_cast<const C2*>(P.qin);
   T.qout = reinterpret_cast<C2*>(P.qout);
   T.y = reinterpret_cast<C2*>(P.y);
+  T.yout = reinterpret_cast<C2*>(P.yout ? P.yout : P.y);
   T.f0 = reinterpret_cast<const C2*>(P.f0);
   T.f1 = reinterpret_cast<const C2*>(P.f1);
   T.f2 = reinterpret_cast<const C2*>(P.f2);
@@ -953,6 +973,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_slab(const SlabParams S) {
                        B.w[2], smem, smem + mapA.total);
   TS.stage = TP.stage = 0;
   TS.h = TP.h = (R)A.h;
+  set_h24(TS, A.h);
+  set_h24(TP, A.h);
   TS.step_k = A.step_k;
   TS.step_wdone = (R)A.step_wdone;
   TS.step_wact = (R)A.step_wact;
@@ -961,6 +983,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_slab(const SlabParams S) {
   TS.src = TP.src = reinterpret_cast<const C2*>(A.src);
   TS.qin = reinterpret_cast<const C2*>(A.qin);
   TS.y = reinterpret_cast<C2*>(A.y);
+  TS.yout = reinterpret_cast<C2*>(A.yout ? A.yout : A.y);
   TS.f0 = reinterpret_cast<const C2*>(A.f0);
   TS.f1 = reinterpret_cast<const C2*>(A.f1);
   TS.f2 = reinterpret_cast<const C2*>(A.f2);
@@ -970,7 +993,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_slab(const SlabParams S) {
   TS.acc = nullptr;
   TP.qin = reinterpret_cast<const C2*>(B.qin);
   TP.qout = reinterpret_cast<C2*>(B.qout);
-  TP.y = nullptr;
+  TP.y = TP.yout = nullptr;
   TP.f0 = TP.f1 = TP.f2 = nullptr;
   TP.fout = TP.pout = TP.acc = nullptr;
   TS.pol_keep = TP.pol_keep = policy_evict_last();
@@ -1055,13 +1078,14 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_batch(BatchLaunc
                        batch_weight(*I, s, 0), batch_weight(*I, s, 1), batch_weight(*I, s, 2), smem);
   T.stage = 0;
   T.h = (R)I->h;
+  set_h24(T, I->h);
   T.step_k = 0;  // clause-by-clause sequences are not batched
   T.step_wdone = T.step_wact = (R)0;
   C2* const* v = reinterpret_cast<C2* const*>(I->vec);
   T.src = v[kVecP];
   T.qin = first ? nullptr : v[kVecQ];
   T.qout = v[kVecQ];
-  T.y = v[kVecY];
+  T.y = T.yout = v[kVecY];
   T.f0 = v[kVecF0 + (int)(n & 3)];
   T.f1 = v[kVecF0 + (int)((n - 1) & 3)];
   T.f2 = v[kVecF0 + (int)((n - 2) & 3)];

@@ -7,6 +7,14 @@ C128, C64 = 0, 1
 TOL_STATE = {C128: 1e-10, C64: 1e-5}  # relative state error bounds of the two precisions
 
 
+def tol_fidelity(prec, psi_ref):
+    """Bar for |P_1 - P_1(oracle)| implied by the state bar: for one amplitude,
+    ||a|^2 - |b|^2| <= (|a| + |b|) |a - b| <= (2 ||b|| + ||a - b||) ||a - b||."""
+    nb = float(np.linalg.norm(psi_ref))
+    d = TOL_STATE[prec] * nb
+    return (2 * nb + d) * d
+
+
 def rel_err(a, b):
     a = np.asarray(a, dtype=np.complex128)
     b = np.asarray(b, dtype=np.complex128)

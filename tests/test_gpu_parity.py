@@ -11,7 +11,7 @@ import pytest
 from instances import generate_ec3, random_state, xx_pairs
 from oracle import oracle as O
 
-from _helpers import C64, C128, TOL_STATE, load_both, random_clauses, random_terms, rel_err
+from _helpers import C64, C128, TOL_STATE, load_both, random_clauses, random_terms, rel_err, tol_fidelity
 
 pytestmark = pytest.mark.gpu
 
@@ -103,7 +103,7 @@ def test_ec3_n10_linear_T20_full_solve(prec):
     assert rel_err(got, ref.psi) < TOL_STATE[prec], rel_err(got, ref.psi)
     assert st["evaluations"] == ref.evaluations
     fid = ctx.fidelity(inst.solution)
-    assert abs(fid - O.fidelity(ref.psi, inst.solution)) < (1e-12 if prec == C128 else 1e-6)
+    assert abs(fid - O.fidelity(ref.psi, inst.solution)) < (1e-12 if prec == C128 else tol_fidelity(prec, ref.psi))
     e = ctx.energy(1)
     assert abs(e - O.energy(H, ref.psi, 1)) < (1e-11 if prec == C128 else 1e-5)
     assert abs(st["norm2"] - O.norm2(ref.psi)) < (1e-12 if prec == C128 else 1e-6)

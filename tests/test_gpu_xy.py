@@ -10,7 +10,7 @@ import pytest
 from instances import generate_ec3
 from oracle import oracle as O
 
-from _helpers import C64, C128, TOL_STATE, rel_err
+from _helpers import C64, C128, TOL_STATE, rel_err, tol_fidelity
 
 pytestmark = pytest.mark.gpu
 
@@ -82,7 +82,8 @@ def test_xy_algorithms_full_solve(prec, driver, alpha):
     # Hamming weight is conserved exactly: amplitudes outside the sector stay zero
     w = np.array([bin(z).count("1") for z in range(1 << 12)])
     assert np.all(psi[w != k] == 0)
-    assert abs(abs(psi[inst.solution]) ** 2 - abs(ref.psi[inst.solution]) ** 2) < (1e-12 if prec == C128 else 1e-6)
+    assert abs(abs(psi[inst.solution]) ** 2 - abs(ref.psi[inst.solution]) ** 2) < (
+        1e-12 if prec == C128 else tol_fidelity(prec, ref.psi))
 
 
 @pytest.mark.parametrize("prec", [C128, C64])
