@@ -345,3 +345,159 @@ fail:
   for (int i = 0; i < 4; i++) free(f[i]);
   return -1;
 }
+
+/* ---- adaptive step size (the paper states no step control; reading: Milne estimate) ----
+ * The integration is a sequence of segments of constant step h.  A segment starting at t0 with
+ * a proposed step hp takes m = ceil((T - t0) / hp) steps of h = (T - t0) / m, so that the last
+ * step of the run lands on T; step k of the segment starts at t0 + k h.  Each segment begins
+ * with up to three classical RK4 steps (accepted without an estimate), then f_3 and PEC steps as
+ * in or_propagate.  A PEC step is accepted if its Milne estimate e = (19/270) ||y_{n+1} - p_{n+1}||
+ * is at most tol ||y_{n+1}||.  A rejected step is discarded and a new segment starts with
+ * hp = h/2: at the step's start, or, for the first PEC step of a segment (whose estimate also
+ * judges the RK4 start-up that built its history), at the segment's own start, the RK4 steps
+ * discarded with it.  After `grow_after` (> 0) accepted PEC steps in a row with
+ * e <= tol ||y_{n+1}|| / 32, a new segment starts at the current time with hp = 2h.  A proposed
+ * step below hmin fails the run (-4). */
+typedef struct {
+  double t0, h;
+  int64_t steps; /* accepted grid steps of the segment */
+  int32_t end;   /* 0 running, 1 reached T, 2 a PEC step was rejected, 3 the step grew */
+  int32_t pad;
+} or_segment;
+
+typedef struct {
+  int64_t steps_done;   /* accepted grid steps (RK4 and PEC) */
+  int64_t evaluations;  /* H|psi> evaluations, rejected steps included */
+  int64_t rejects;      /* rejected PEC steps */
+  int64_t segments;     /* segments begun */
+  int64_t pec_attempts; /* PEC steps tried (accepted and rejected) */
+  double max_err_est;   /* max of e over accepted PEC steps */
+  double t_end;
+} or_astats;
+
+/* m = ceil(R / hp), with R / hp a hair above an integer (rounding of hp = R / N) counted as
+ * that integer, so a proposed step of exactly R / N gives N steps */
+static int64_t segment_steps(double R, double hp) {
+  double q = ceil((R / hp) * (1.0 - 1e-12));
+  return q < 1.0 ? 1 : (int64_t)q;
+}
+
+/* ratio_log (may be NULL): e / (tol ||y_{n+1}||) of every PEC attempt, up to ratio_cap entries */
+int or_propagate_adaptive(const or_ham *H, const or_sched *sc, double h0, double tol, int grow_after, double hmin,
+                          int64_t max_steps, double *psi, or_astats *st, or_segment *log, int64_t log_cap,
+                          double *ratio_log, int64_t ratio_cap, int nthreads) {
+  uint64_t N = 1ull << H->n;
+  size_t bytes = sizeof(double) * 2 * N;
+  if (!(h0 > 0.0) || !(tol > 0.0) || !(hmin > 0.0)) return -2;
+  double *f[4], *tmp = (double *)malloc(bytes), *ys = (double *)malloc(bytes), *k = (double *)malloc(bytes),
+         *acc = (double *)malloc(bytes), *p = (double *)malloc(bytes), *ynew = (double *)malloc(bytes),
+         *yseg = (double *)malloc(bytes); /* the state at the segment's start */
+  for (int i = 0; i < 4; i++) f[i] = (double *)malloc(bytes);
+  int bad = !tmp || !ys || !k || !acc || !p || !ynew || !yseg, rc = 0;
+  for (int i = 0; i < 4; i++) bad |= !f[i];
+  memset(st, 0, sizeof(*st));
+  if (bad) { rc = -1; goto out; }
+
+  double t0 = 0.0, hp = h0, h = 0.0;
+  int64_t m = 0, kk = 0; /* steps in the segment, index of the next step */
+  int small_run = 0, restart = 1, have_hist = 0;
+  int64_t cur = -1;      /* log entry of the current segment */
+  int64_t seg_done = 0;  /* accepted steps before the current segment */
+  while (max_steps < 0 || st->steps_done < max_steps) {
+    if (restart) {
+      if (hp < hmin) { rc = -4; break; }
+      double R = sc->T - t0;
+      m = segment_steps(R, hp);
+      h = R / (double)m;
+      kk = 0;
+      small_run = 0;
+      have_hist = 0;
+      restart = 0;
+      memcpy(yseg, psi, bytes);
+      seg_done = st->steps_done;
+      st->segments++;
+      cur = st->segments - 1;
+      if (cur < log_cap) {
+        log[cur].t0 = t0; log[cur].h = h; log[cur].steps = 0; log[cur].end = 0; log[cur].pad = 0;
+      }
+    }
+    if (kk >= m) break;
+    double t = t0 + (double)kk * h;
+    if (kk < 3) {
+      /* classical RK4 step; k1 is the history value f_kk */
+      if (deriv(H, sc, t, psi, f[kk], tmp, N, nthreads)) { rc = -1; break; }
+      for (uint64_t i = 0; i < 2 * N; i++) acc[i] = f[kk][i];
+      for (uint64_t i = 0; i < 2 * N; i++) ys[i] = psi[i] + 0.5 * h * f[kk][i];
+      if (deriv(H, sc, t + 0.5 * h, ys, k, tmp, N, nthreads)) { rc = -1; break; }
+      for (uint64_t i = 0; i < 2 * N; i++) acc[i] += 2.0 * k[i];
+      for (uint64_t i = 0; i < 2 * N; i++) ys[i] = psi[i] + 0.5 * h * k[i];
+      if (deriv(H, sc, t + 0.5 * h, ys, k, tmp, N, nthreads)) { rc = -1; break; }
+      for (uint64_t i = 0; i < 2 * N; i++) acc[i] += 2.0 * k[i];
+      for (uint64_t i = 0; i < 2 * N; i++) ys[i] = psi[i] + h * k[i];
+      if (deriv(H, sc, t + h, ys, k, tmp, N, nthreads)) { rc = -1; break; }
+      for (uint64_t i = 0; i < 2 * N; i++) acc[i] += k[i];
+      for (uint64_t i = 0; i < 2 * N; i++) psi[i] += (h / 6.0) * acc[i];
+      st->evaluations += 4;
+      st->steps_done++;
+      kk++;
+      if (cur < log_cap) log[cur].steps++;
+      if (kk == m && cur < log_cap) log[cur].end = 1;
+      continue;
+    }
+    if (!have_hist) { /* f_3 = f(t_3, y_3) */
+      if (deriv(H, sc, t, psi, f[3], tmp, N, nthreads)) { rc = -1; break; }
+      st->evaluations++;
+      have_hist = 1;
+    }
+    const double *fn = f[kk & 3], *fn1 = f[(kk - 1) & 3], *fn2 = f[(kk - 2) & 3], *fn3 = f[(kk - 3) & 3];
+    for (uint64_t i = 0; i < 2 * N; i++)
+      p[i] = psi[i] + (h / 24.0) * (55.0 * fn[i] - 59.0 * fn1[i] + 37.0 * fn2[i] - 9.0 * fn3[i]);
+    double *fnew = f[(kk + 1) & 3];
+    if (deriv(H, sc, t0 + (double)(kk + 1) * h, p, fnew, tmp, N, nthreads)) { rc = -1; break; }
+    st->evaluations++;
+    double e2 = 0.0, y2 = 0.0;
+    for (uint64_t i = 0; i < 2 * N; i++) {
+      ynew[i] = psi[i] + (h / 24.0) * (9.0 * fnew[i] + 19.0 * fn[i] - 5.0 * fn1[i] + fn2[i]);
+      e2 += (ynew[i] - p[i]) * (ynew[i] - p[i]);
+      y2 += ynew[i] * ynew[i];
+    }
+    double est = (19.0 / 270.0) * sqrt(e2), lim = tol * sqrt(y2);
+    if (ratio_log && st->pec_attempts < ratio_cap) ratio_log[st->pec_attempts] = est / lim;
+    st->pec_attempts++;
+    if (!(est <= lim)) { /* reject: a new segment with half the step */
+      st->rejects++;
+      if (cur < log_cap) log[cur].end = 2;
+      if (kk == 3) { /* the first PEC step: the segment's start-up goes too */
+        memcpy(psi, yseg, bytes);
+        st->steps_done = seg_done;
+        if (cur < log_cap) log[cur].steps = 0;
+      } else {
+        t0 = t;
+      }
+      hp = 0.5 * h;
+      restart = 1;
+      continue;
+    }
+    memcpy(psi, ynew, bytes);
+    if (est > st->max_err_est) st->max_err_est = est;
+    st->steps_done++;
+    kk++;
+    if (cur < log_cap) log[cur].steps++;
+    if (kk == m) {
+      if (cur < log_cap) log[cur].end = 1;
+      continue;
+    }
+    small_run = est <= lim / 32.0 ? small_run + 1 : 0;
+    if (grow_after > 0 && small_run >= grow_after) { /* the step grows: new segment from here */
+      if (cur < log_cap) log[cur].end = 3;
+      t0 = t0 + (double)kk * h;
+      hp = 2.0 * h;
+      restart = 1;
+    }
+  }
+  st->t_end = (kk >= m && m > 0) ? t0 + (double)m * h : t0 + (double)kk * h;
+out:
+  free(tmp); free(ys); free(k); free(acc); free(p); free(ynew); free(yseg);
+  for (int i = 0; i < 4; i++) free(f[i]);
+  return rc;
+}

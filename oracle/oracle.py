@@ -86,6 +86,22 @@ class _Stats(C.Structure):
     ]
 
 
+class _AStats(C.Structure):
+    _fields_ = [
+        ("steps_done", C.c_int64),
+        ("evaluations", C.c_int64),
+        ("rejects", C.c_int64),
+        ("segments", C.c_int64),
+        ("pec_attempts", C.c_int64),
+        ("max_err_est", C.c_double),
+        ("t_end", C.c_double),
+    ]
+
+
+class _Segment(C.Structure):
+    _fields_ = [("t0", C.c_double), ("h", C.c_double), ("steps", C.c_int64), ("end", C.c_int32), ("pad", C.c_int32)]
+
+
 def _load():
     global _lib
     if _lib is None:
@@ -98,6 +114,10 @@ def _load():
         lib.or_hpsi_at.argtypes = [C.POINTER(_Ham), C.POINTER(C.c_double), C.c_void_p, C.c_int64, C.c_void_p,
                                    C.c_void_p]
         lib.or_hpsi_at.restype = C.c_int
+        lib.or_propagate_adaptive.argtypes = [C.POINTER(_Ham), C.POINTER(_Sched), C.c_double, C.c_double, C.c_int,
+                                              C.c_double, C.c_int64, C.c_void_p, C.POINTER(_AStats),
+                                              C.POINTER(_Segment), C.c_int64, C.c_void_p, C.c_int64, C.c_int]
+        lib.or_propagate_adaptive.restype = C.c_int
         lib.or_weights.argtypes = [C.POINTER(_Sched), C.c_double, C.POINTER(C.c_double)]
         lib.or_weights.restype = None
         _lib = lib
@@ -378,6 +398,46 @@ def propagate(H: Hamiltonian, sched: Schedule, nsteps: int, psi0, max_steps: int
     if rc != 0:
         raise RuntimeError(f"or_propagate failed ({rc})")
     return PropagateResult(psi, st.steps_done, st.evaluations, st.max_err_est, st.last_err_est, st.t_end)
+
+
+SEG_RUNNING, SEG_AT_T, SEG_REJECTED, SEG_GREW = 0, 1, 2, 3
+
+
+@dataclass
+class AdaptiveResult:
+    psi: np.ndarray
+    steps_done: int
+    evaluations: int
+    rejects: int
+    max_err_est: float
+    t_end: float
+    segments: list  # (t0, h, accepted steps, end) per segment of constant step
+    ratios: np.ndarray  # Milne estimate / (tol ||y||) of every PEC attempt (accepted iff <= 1)
+
+
+def propagate_adaptive(H: Hamiltonian, sched: Schedule, h0, tol, psi0, grow_after=16, hmin=None, max_steps=-1,
+                       nthreads=1, log_cap=100000):
+    """Integrate with step-size control (or_propagate_adaptive): segments of constant h that
+    land on T, a PEC step accepted if its Milne estimate <= tol ||y||, otherwise a new segment
+    with h/2; 2h after `grow_after` accepted steps with estimates <= tol ||y|| / 32."""
+    lib = _load()
+    psi = np.array(psi0, dtype=np.complex128, copy=True)
+    if psi.shape != (1 << H.n,):
+        raise ValueError("psi0 must have 2**n entries")
+    h, keep = H._ctypes()
+    sc = sched._ctypes()
+    st = _AStats()
+    log = (_Segment * log_cap)()
+    hmin = float(h0) * 2.0 ** -30 if hmin is None else float(hmin)
+    ratios = np.zeros(log_cap)
+    rc = lib.or_propagate_adaptive(C.byref(h), C.byref(sc), float(h0), float(tol), int(grow_after), hmin,
+                                   int(max_steps), psi.ctypes.data, C.byref(st), log, int(log_cap),
+                                   ratios.ctypes.data, int(log_cap), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"or_propagate_adaptive failed ({rc})")
+    segs = [(log[i].t0, log[i].h, log[i].steps, log[i].end) for i in range(min(st.segments, log_cap))]
+    ratios = ratios[: min(log_cap, st.pec_attempts)]
+    return AdaptiveResult(psi, st.steps_done, st.evaluations, st.rejects, st.max_err_est, st.t_end, segs, ratios)
 
 
 def uniform_state(n):
