@@ -8,8 +8,9 @@
  * (Sec. I.A, Eq. SQH-Hamiltonian): a list of Pauli products with real prefactors, plus
  * Exact-Cover-3 clause penalties (Eq. hci, Eq. sat).  The integrator is a fourth-order
  * predictor-corrector with one H|psi> per step (Sec. I.B): Adams-Bashforth-4 predictor,
- * Adams-Moulton-4 corrector in PEC mode, fixed step h = T/N, started by three classical
- * Runge-Kutta-4 steps.  All arithmetic runs in CUDA kernels for sm_103a.
+ * Adams-Moulton-4 corrector in PEC mode, fixed step h = T/N or step-size control on the
+ * corrector's Milne estimate, started by three classical Runge-Kutta-4 steps.  All arithmetic
+ * runs in CUDA kernels for sm_103a.
  *
  * Conventions (all entry points)
  *   - Return value: AQC_OK (0) or a negative AQC_E_* code; the context keeps a message
@@ -44,6 +45,9 @@ extern "C" {
 #define AQC_E_NUMERIC (-4)      /* non-finite value detected in a reduction               */
 #define AQC_E_STATE (-5)        /* call out of order (e.g. propagate before a schedule)   */
 #define AQC_E_UNSUPPORTED (-6)  /* a term no layout can hold, or a size beyond the limits */
+#define AQC_E_TIMEOUT (-7)      /* a bounded wait inside a kernel gave up (a tile copy that
+                                   never landed, a partial sum that never came): that call's
+                                   results are invalid; the context stays usable            */
 
 #define AQC_C128 0 /* complex128 state, FP64 arithmetic                                   */
 #define AQC_C64 1  /* complex64 state, FP32 arithmetic, FP64 reductions                   */
@@ -68,17 +72,33 @@ extern "C" {
 typedef struct aqc_ctx aqc_ctx;
 
 typedef struct {
-  int64_t steps_done;  /* grid steps completed since the initial state was set          */
-  int64_t n_steps;     /* N of the grid h = T/N                                          */
-  int64_t evaluations; /* H|psi> evaluations so far                                      */
-  double t;            /* current time (steps_done * h)                                  */
-  double h;            /* step size                                                      */
+  int64_t steps_done;  /* accepted grid steps since the initial state was set            */
+  int64_t n_steps;     /* N of the grid h = T/N (step-size control: steps_done plus the
+                          steps left in the current segment)                             */
+  int64_t evaluations; /* H|psi> evaluations so far (rejected steps included)            */
+  double t;            /* current time                                                   */
+  double h;            /* current step size                                              */
   double norm2;        /* ||psi||^2 after the call (FP64 reduction)                      */
-  double max_err_est;  /* max over PEC steps of (19/270) ||y_{n+1} - p_{n+1}||           */
+  double max_err_est;  /* max over accepted PEC steps of (19/270) ||y_{n+1} - p_{n+1}||  */
   double last_err_est; /* the same for the last PEC step                                 */
   double elapsed_ms;   /* device time of the call (CUDA events on the context stream)    */
   int64_t launches;    /* kernel launches this call issued                               */
+  int64_t rejects;     /* PEC steps rejected by the step-size control since the initial state */
+  int64_t segments;    /* segments of constant step begun since the initial state         */
 } aqc_stats;
+
+/* One segment of constant step size of a run (aqc_get_segments). */
+#define AQC_SEG_RUNNING 0  /* the current segment                                           */
+#define AQC_SEG_AT_T 1     /* its last step landed on T                                     */
+#define AQC_SEG_REJECTED 2 /* a PEC step was rejected: the next segment starts there, h/2    */
+#define AQC_SEG_GREW 3     /* small estimates: the next segment starts here with 2h          */
+typedef struct {
+  double t0;     /* start time                                                              */
+  double h;      /* step size                                                               */
+  int64_t steps; /* accepted grid steps                                                     */
+  int32_t end;   /* AQC_SEG_*                                                               */
+  int32_t pad;
+} aqc_segment;
 
 /* ---- lifetime ---------------------------------------------------------------------- */
 
@@ -86,6 +106,12 @@ typedef struct {
  * vectors (y, p, q, four derivative slots f, one Runge-Kutta accumulator) plus tables and
  * reduction slots.  Returns 0 for unsupported arguments. */
 size_t aqc_workspace_bytes(int n_qubits, int precision);
+
+/* The same with options: AQC_WS_STEP_CONTROL adds one state-sized vector (the state at the
+ * start of a segment of constant step), which step-size control (aqc_set_integrator with
+ * adaptive = 1) needs.  Returns 0 for unsupported arguments or unknown flags. */
+#define AQC_WS_STEP_CONTROL 1u
+size_t aqc_workspace_bytes_ex(int n_qubits, int precision, unsigned flags);
 
 /* Create a context on `device` for n_qubits with state precision AQC_C128 or AQC_C64.
  * `workspace` is a caller-owned device pointer (256-byte aligned) of at least
@@ -134,11 +160,35 @@ int aqc_set_schedule(aqc_ctx *ctx, int s_kind, double T, const double coefA[4], 
 
 /* ---- integrator (Sec. I.B) ----------------------------------------------------------- */
 
-/* Fixed-step grid h = T/N.  n_steps > 0 sets N; n_steps == 0 applies the step rule
+/* Step grid.  n_steps > 0 sets N; n_steps == 0 applies the step rule
  * N = max(4, ceil(T * Lambda / kappa)), Lambda = max over s in [0,1] (1025-point grid) of
  * sum_g |w_g(s)| * ||H_g||_1 (sum of |prefactors| + max clause penalties), with kappa > 0
- * (0 selects 0.1; the PEC scheme is stable on the imaginary axis up to about 0.22). */
-int aqc_set_integrator(aqc_ctx *ctx, int64_t n_steps, double kappa);
+ * (0 selects 0.1; the PEC scheme is stable on the imaginary axis up to about 0.22).
+ * adaptive = 0: the fixed-step grid h = T/N (tol ignored).
+ * adaptive = 1: step-size control on the Milne estimate of Sec. I.B's predictor-corrector (the
+ * paper states no control rule; this is the library's).  The run is a sequence of segments of
+ * constant step h that each start with up to three RK4 steps; the first segment has the grid
+ * step T/N.  A PEC step is accepted if (19/270) ||y_{n+1} - p_{n+1}|| <= tol ||y_{n+1}||; a
+ * rejected step is discarded and a new segment starts at that step's start with h' = h/2.
+ * After grow_after (aqc_set_step_growth, default 16) accepted PEC steps in a row with an
+ * estimate <= tol ||y|| / 32, a new segment starts with h' = 2h.  A segment from t0 with
+ * proposed step h' takes m = ceil((T - t0) / h') steps of (T - t0) / m, so the run lands on T.
+ * The first PEC step of a segment also judges the RK4 start-up that built its history: if it
+ * is rejected, the whole segment is redone from its own start with h/2.  Needs a workspace of
+ * aqc_workspace_bytes_ex(n, precision, AQC_WS_STEP_CONTROL) bytes (else AQC_E_NOMEM).
+ * Each PEC step reads two numbers back to the host (one synchronisation per step).  A step
+ * below 2^-30 T/N fails with AQC_E_NUMERIC.  tol must be positive for adaptive = 1.  Resets
+ * the integration (a new initial state is needed).  A context under step-size control cannot
+ * join a batch. */
+int aqc_set_integrator(aqc_ctx *ctx, int64_t n_steps, double kappa, int adaptive, double tol);
+
+/* Consecutive small-estimate PEC steps before the step grows (0 = never grows). */
+int aqc_set_step_growth(aqc_ctx *ctx, int grow_after);
+
+/* The segments of constant step of the run so far (since the last initial state), in order:
+ * up to max_out entries into out[], their total number into *count (may be NULL).  The fixed-
+ * step grid is one segment. */
+int aqc_get_segments(aqc_ctx *ctx, aqc_segment *out, int64_t max_out, int64_t *count);
 
 /* The step grid the next (or current) propagation uses: N and h = T/N (step rule above). */
 int aqc_get_grid(aqc_ctx *ctx, int64_t *n_steps, double *h);
@@ -169,7 +219,7 @@ int aqc_set_relabel(aqc_ctx *ctx, int enable);
  * fewer bytes per step at 28 qubits but runs slower than the separate passes, hence off.  Results equal those of the layer order up
  * to the rounding of the partial sums' summation order.  The step's CTAs wait for the partial
  * tiles of their slab with a bounded poll; a wait that gives up (only possible after a fault
- * elsewhere) makes the next aqc_propagate with stats return AQC_E_CUDA.  Does not reset the
+ * elsewhere) makes the next aqc_propagate with stats return AQC_E_TIMEOUT.  Does not reset the
  * integrator. */
 int aqc_set_slab_bits(aqc_ctx *ctx, int slab_bits);
 
@@ -224,9 +274,13 @@ int aqc_transfer_wait(aqc_ctx *ctx);
 /* |<w|psi>|^2, the success probability P_1 of the solution w (Sec. II.B). */
 int aqc_fidelity(aqc_ctx *ctx, uint64_t w, double *out);
 
-/* <psi|H_group|psi> with unit weight on that group (the final energy E(T) of Sec. II.B
- * for the group holding H_f).  Not divided by ||psi||^2. */
-int aqc_energy(aqc_ctx *ctx, int group, double *out);
+/* <psi| sum_{g in group_mask} w_g H_g |psi>, not divided by ||psi||^2: bit g of group_mask
+ * (1..7) selects group g (1 << AQC_GRP_B alone: the final energy E(T) of Sec. II.B when group B
+ * holds H_f).  t >= 0: w_g = the group weight at time t, so group_mask = 7 gives <H(t)>;
+ * t = AQC_UNIT_WEIGHTS (any t < 0): w_g = 1 for every selected group.  A clause-by-clause
+ * sequence (Eq. kpath) takes its coefficients at t (at the current time for unit weights). */
+#define AQC_UNIT_WEIGHTS (-1.0)
+int aqc_energy(aqc_ctx *ctx, int group_mask, double t, double *out);
 
 /* ||psi||^2 (FP64 accumulation). */
 int aqc_norm2(aqc_ctx *ctx, double *out);
@@ -299,6 +353,25 @@ size_t aqc_lanczos_workspace_bytes(int n_qubits, int precision, int max_iter);
  * call); synchronises the context stream. */
 int aqc_lanczos(aqc_ctx *ctx, double t, const void *start, void *work, size_t work_bytes, int max_iter, int n_eig,
                 double tol, double *eig, double *conv, int *iters_out);
+
+/* The lowest eigenpair (theta, x) of H(t) reachable from `start`, by the Lanczos iteration of
+ * aqc_lanczos run until the Ritz residual beta_k |s_k| (from the recurrence, checked every 4
+ * steps) is at most tol * max(1, |theta|), the Krylov space is invariant, or max_iter steps.  For a
+ * Hamiltonian that conserves the Hamming weight and a start inside one weight sector, x is that
+ * sector's ground state: the initial state of the XY algorithm is the ground state of Eq. Hixy in
+ * the solution's sector (Sec. II.A).  x (unit norm, qubit order, state precision, phase chosen so
+ * that <start|x> > 0) goes to the caller's device vector ground_out (2^n amplitudes, 16-byte
+ * aligned); *theta_out gets theta, *resid_out (may be NULL) the residual ||H x - theta x|| of
+ * the returned x, computed with one more H*x, *iters_out (may be NULL) the steps taken.  `work`
+ * as for aqc_lanczos (aqc_lanczos_workspace_bytes).  Uses the context's partial-sum and scratch
+ * vectors (not during a propagation call); synchronises the context stream. */
+int aqc_lanczos_ground(aqc_ctx *ctx, double t, const void *start, void *work, size_t work_bytes, int max_iter,
+                       double tol, double *theta_out, double *resid_out, void *ground_out, int *iters_out);
+
+/* Host helper (no device work): the unit eigenvector, first entry >= 0, of the symmetric
+ * tridiagonal matrix (a[0..k), b[0..k-1)) for its eigenvalue lam (inverse iteration with a
+ * row-pivoted LU of T - lam I, three sweeps); the Ritz coefficients of aqc_lanczos_ground. */
+int aqc_tridiag_eigvec(int k, const double *a, const double *b, double lam, double *out);
 
 /* Host helper (no device work): the n_eig lowest eigenvalues, ascending, of the symmetric
  * tridiagonal matrix with diagonal a[0..k) and off-diagonal b[0..k-1), by Sturm-sequence

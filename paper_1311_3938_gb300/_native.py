@@ -20,6 +20,10 @@ AQC_E_CUDA = -3
 AQC_E_NUMERIC = -4
 AQC_E_STATE = -5
 AQC_E_UNSUPPORTED = -6
+AQC_E_TIMEOUT = -7
+AQC_UNIT_WEIGHTS = -1.0
+AQC_SEG_RUNNING, AQC_SEG_AT_T, AQC_SEG_REJECTED, AQC_SEG_GREW = 0, 1, 2, 3
+AQC_WS_STEP_CONTROL = 1
 
 AQC_C128 = 0
 AQC_C64 = 1
@@ -49,10 +53,16 @@ class aqc_stats(C.Structure):
         ("last_err_est", C.c_double),
         ("elapsed_ms", C.c_double),
         ("launches", C.c_int64),
+        ("rejects", C.c_int64),
+        ("segments", C.c_int64),
     ]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class aqc_segment(C.Structure):
+    _fields_ = [("t0", C.c_double), ("h", C.c_double), ("steps", C.c_int64), ("end", C.c_int32), ("pad", C.c_int32)]
 
 
 _lib = None
@@ -68,6 +78,7 @@ def lib():
         vp, i32, i64, u64, dbl, sz = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double, C.c_size_t
         sig = {
             "aqc_workspace_bytes": (sz, [i32, i32]),
+            "aqc_workspace_bytes_ex": (sz, [i32, i32, C.c_uint]),
             "aqc_create": (i32, [C.POINTER(vp), i32, i32, i32, vp, sz, vp]),
             "aqc_destroy": (None, [vp]),
             "aqc_set_stream": (i32, [vp, vp]),
@@ -75,7 +86,9 @@ def lib():
             "aqc_load_clauses": (i32, [vp, i32, sz, vp, i32, dbl]),
             "aqc_clear_hamiltonian": (i32, [vp]),
             "aqc_set_schedule": (i32, [vp, i32, dbl, vp, vp, vp]),
-            "aqc_set_integrator": (i32, [vp, i64, dbl]),
+            "aqc_set_integrator": (i32, [vp, i64, dbl, i32, dbl]),
+            "aqc_set_step_growth": (i32, [vp, i32]),
+            "aqc_get_segments": (i32, [vp, C.POINTER(aqc_segment), i64, C.POINTER(i64)]),
             "aqc_set_tile_bits": (i32, [vp, i32]),
             "aqc_set_slab_bits": (i32, [vp, i32]),
             "aqc_set_relabel": (i32, [vp, i32]),
@@ -88,13 +101,16 @@ def lib():
             "aqc_fetch_state": (i32, [vp, vp]),
             "aqc_transfer_wait": (i32, [vp]),
             "aqc_fidelity": (i32, [vp, u64, C.POINTER(dbl)]),
-            "aqc_energy": (i32, [vp, i32, C.POINTER(dbl)]),
+            "aqc_energy": (i32, [vp, i32, dbl, C.POINTER(dbl)]),
             "aqc_norm2": (i32, [vp, C.POINTER(dbl)]),
             "aqc_hpsi": (i32, [vp, dbl, vp, vp]),
             "aqc_lanczos_workspace_bytes": (sz, [i32, i32, i32]),
             "aqc_lanczos": (i32, [vp, dbl, vp, vp, sz, i32, i32, dbl, C.POINTER(dbl), C.POINTER(dbl),
                                   C.POINTER(i32)]),
+            "aqc_lanczos_ground": (i32, [vp, dbl, vp, vp, sz, i32, dbl, C.POINTER(dbl), C.POINTER(dbl), vp,
+                                         C.POINTER(i32)]),
             "aqc_tridiag_eigvals": (i32, [i32, C.POINTER(dbl), C.POINTER(dbl), i32, C.POINTER(dbl)]),
+            "aqc_tridiag_eigvec": (i32, [i32, C.POINTER(dbl), C.POINTER(dbl), dbl, C.POINTER(dbl)]),
             "aqc_launch_count": (i32, [vp, C.POINTER(i64)]),
             "aqc_batch_workspace_bytes": (sz, [i32, i64]),
             "aqc_batch_create": (i32, [C.POINTER(vp), i32, i32, i32, i64, vp, sz, vp]),
@@ -136,6 +152,10 @@ def aqc_workspace_bytes(n_qubits: int, precision: int) -> int:
     return int(lib().aqc_workspace_bytes(n_qubits, precision))
 
 
+def aqc_workspace_bytes_ex(n_qubits: int, precision: int, flags: int) -> int:
+    return int(lib().aqc_workspace_bytes_ex(n_qubits, precision, int(flags)))
+
+
 def aqc_create(device: int, precision: int, n_qubits: int, workspace: int, workspace_bytes: int, stream: int):
     h = C.c_void_p()
     rc = lib().aqc_create(C.byref(h), device, precision, n_qubits, C.c_void_p(workspace), workspace_bytes,
@@ -169,8 +189,21 @@ def aqc_set_schedule(ctx, s_kind, T, coefA, coefB, coefC):
     _check(ctx, lib().aqc_set_schedule(ctx, s_kind, float(T), arr[0], arr[1], arr[2]))
 
 
-def aqc_set_integrator(ctx, n_steps, kappa):
-    _check(ctx, lib().aqc_set_integrator(ctx, int(n_steps), float(kappa)))
+def aqc_set_integrator(ctx, n_steps, kappa, adaptive=0, tol=0.0):
+    _check(ctx, lib().aqc_set_integrator(ctx, int(n_steps), float(kappa), int(adaptive), float(tol)))
+
+
+def aqc_set_step_growth(ctx, grow_after):
+    _check(ctx, lib().aqc_set_step_growth(ctx, int(grow_after)))
+
+
+def aqc_get_segments(ctx):
+    """[(t0, h, steps, end)] of the segments of constant step of the run so far."""
+    count = C.c_int64()
+    _check(ctx, lib().aqc_get_segments(ctx, None, 0, C.byref(count)))
+    arr = (aqc_segment * max(1, count.value))()
+    _check(ctx, lib().aqc_get_segments(ctx, arr, count.value, C.byref(count)))
+    return [(arr[i].t0, arr[i].h, arr[i].steps, arr[i].end) for i in range(count.value)]
 
 
 def aqc_get_grid(ctx):
@@ -228,9 +261,9 @@ def aqc_fidelity(ctx, w):
     return out.value
 
 
-def aqc_energy(ctx, group):
+def aqc_energy(ctx, group_mask, t=AQC_UNIT_WEIGHTS):
     out = C.c_double()
-    _check(ctx, lib().aqc_energy(ctx, int(group), C.byref(out)))
+    _check(ctx, lib().aqc_energy(ctx, int(group_mask), float(t), C.byref(out)))
     return out.value
 
 
@@ -258,6 +291,17 @@ def aqc_lanczos(ctx, t, start_ptr, work_ptr, work_bytes, max_iter, n_eig, tol):
     return list(eig), list(conv), iters.value
 
 
+def aqc_lanczos_ground(ctx, t, start_ptr, work_ptr, work_bytes, max_iter, tol, ground_ptr):
+    """(theta, residual, iterations); the unit ground vector is written to ground_ptr."""
+    theta = C.c_double()
+    resid = C.c_double()
+    iters = C.c_int()
+    _check(ctx, lib().aqc_lanczos_ground(ctx, float(t), C.c_void_p(start_ptr), C.c_void_p(work_ptr), int(work_bytes),
+                                         int(max_iter), float(tol), C.byref(theta), C.byref(resid),
+                                         C.c_void_p(ground_ptr), C.byref(iters)))
+    return theta.value, resid.value, iters.value
+
+
 def aqc_tridiag_eigvals(a, b, n_eig):
     k = len(a)
     A = (C.c_double * k)(*a)
@@ -266,6 +310,17 @@ def aqc_tridiag_eigvals(a, b, n_eig):
     rc = lib().aqc_tridiag_eigvals(k, A, B, int(n_eig), out)
     if rc:
         raise AqcError(rc, "aqc_tridiag_eigvals: bad arguments")
+    return list(out)
+
+
+def aqc_tridiag_eigvec(a, b, lam):
+    k = len(a)
+    A = (C.c_double * k)(*a)
+    B = (C.c_double * max(1, k - 1))(*b) if k > 1 else (C.c_double * 1)()
+    out = (C.c_double * k)()
+    rc = lib().aqc_tridiag_eigvec(k, A, B, float(lam), out)
+    if rc:
+        raise AqcError(rc, "aqc_tridiag_eigvec: bad arguments")
     return list(out)
 
 

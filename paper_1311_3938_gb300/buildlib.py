@@ -13,7 +13,9 @@ LIB = os.path.join(BUILD, "libaqc.so")
 SOURCES = ["api.cu", "kernels.cu", "xpartial.cu", "lanczos.cu", "noalloc.cu"]
 HEADERS = ["aqc_internal.h", os.path.join("..", "..", "include", "aqc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# host code without contracted multiply-adds: its FP64 arithmetic (step times, schedule
+# weights, segment plans) rounds the same on x86 and Arm, each operation rounded on its own
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-ffp-contract=off"]
 
 
 def nvcc() -> str:

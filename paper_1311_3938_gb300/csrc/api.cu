@@ -91,7 +91,7 @@ struct WsPlan {
   size_t partial_doubles;
 };
 
-WsPlan plan_workspace(int n, int prec) {
+WsPlan plan_workspace(int n, int prec, unsigned flags = 0) {
   WsPlan w;
   const size_t amp = prec == AQC_C128 ? 16 : 8;
   w.off_tab = 0;
@@ -106,7 +106,8 @@ WsPlan plan_workspace(int n, int prec) {
   w.off_dcode = align_up(w.off_partials + w.partial_doubles * sizeof(double), 256);
   w.off_vec = align_up(w.off_dcode + ((size_t)1 << n), 256);
   w.vec_bytes = align_up(((size_t)1 << n) * amp, 256);
-  w.total = w.off_vec + V_COUNT * w.vec_bytes;
+  // AQC_WS_STEP_CONTROL: one more vector, the state at the start of a segment of constant step
+  w.total = w.off_vec + (V_COUNT + ((flags & AQC_WS_STEP_CONTROL) ? 1 : 0)) * w.vec_bytes;
   return w;
 }
 
@@ -168,8 +169,26 @@ struct aqc_ctx {
 
   bool have_state = false;
   bool hist_ready = false;
+  // The run is a sequence of segments of constant step h: the current one starts at seg_t0 and
+  // has seg_m steps; `step` is the step index inside it (it selects the RK4 start-up for
+  // step < 3 and the derivative ring slot).  The fixed-step grid is one segment from t = 0.
   int64_t step = 0, nsteps = 0, evals = 0;
   double h = 0;
+  double seg_t0 = 0.0;
+  int64_t seg_m = 0;
+  int64_t steps_done = 0;   // accepted grid steps since the initial state, all segments
+  bool at_end = false;      // the last step of the run landed on T
+  // step-size control (aqc_set_integrator with adaptive = 1)
+  int adaptive = 0;
+  double tol = 0.0;
+  int grow_after = 16;
+  int small_run = 0;        // accepted PEC steps in a row with an estimate <= tol ||y|| / 32
+  int64_t rejects = 0;
+  double max_err_acc = 0.0; // max estimate over accepted PEC steps
+  double hmin = 0.0;
+  void* vec_save = nullptr; // state at the start of the current segment (AQC_WS_STEP_CONTROL)
+  int64_t seg_done0 = 0;    // accepted steps before the current segment
+  std::vector<aqc_segment> segs;
   int64_t launches = 0;  // kernel launches issued (monotone counter)
 
   std::string err;
@@ -744,7 +763,7 @@ int ensure_ready(aqc_ctx* c) {
 }
 
 int rk4_step(aqc_ctx* c) {
-  const double t = (double)c->step * c->h, hh = c->h;
+  const double t = c->seg_t0 + (double)c->step * c->h, hh = c->h;
   double w[3];
   for (int stage = 1; stage <= 4; stage++) {
     const double ts = stage == 1 ? t : (stage == 4 ? t + hh : t + 0.5 * hh);
@@ -761,14 +780,13 @@ int rk4_step(aqc_ctx* c) {
     if (rc) return rc;
     c->evals++;
   }
-  c->step++;
-  return AQC_OK;
+  return AQC_OK;  // the caller counts the step (count_step)
 }
 
 int start_history(aqc_ctx* c) {
   // f_3 = -i H(t_3) y_3, then p_4 from the AB4 predictor
   double w[3];
-  sched_weights(c, 3.0 * c->h, w);
+  sched_weights(c, c->seg_t0 + 3.0 * c->h, w);
   ApplyParams fin = base_params(c);
   fin.mode = MODE_DERIV;
   fin.fout = c->vec[V_F0 + 3];
@@ -822,7 +840,7 @@ int pec_step_slabs(aqc_ctx* c, const double w[3], const ApplyParams& fin) {
 int pec_step(aqc_ctx* c) {
   const int64_t n = c->step;
   double w[3];
-  sched_weights(c, (double)(n + 1) * c->h, w);
+  sched_weights(c, c->seg_t0 + (double)(n + 1) * c->h, w);
   ApplyParams fin = base_params(c);
   fin.mode = MODE_STEP;
   fin.h = c->h;
@@ -832,10 +850,95 @@ int pec_step(aqc_ctx* c) {
   fin.f2 = c->vec[V_F0 + (int)((n - 2) & 3)];
   fin.fout = c->vec[V_F0 + (int)((n + 1) & 3)];
   fin.pout = c->vec[V_P];
+  // under step-size control y_{n+1} goes to the scratch vector, so a rejected step keeps y_n
+  fin.yout = c->adaptive ? c->vec[V_ACC] : nullptr;
   int rc = c->slab.n_slabs ? pec_step_slabs(c, w, fin) : evaluate(c, w, c->vec[V_P], fin, nullptr);
   if (rc) return rc;
   c->evals++;
+  return AQC_OK;  // the caller counts the step (count_step) or decides on it (control_step)
+}
+
+// m = ceil(R / hp) steps of h = R / m for a segment of length R, a ratio a hair above an integer
+// (the rounding of hp = R / N) counted as that integer
+int64_t segment_steps(double R, double hp) {
+  const double q = ceil((R / hp) * (1.0 - 1e-12));
+  return q < 1.0 ? 1 : (int64_t)q;
+}
+
+// A new segment of constant step from t0 with proposed step hp (it lands on T).
+int begin_segment(aqc_ctx* c, double t0, double hp, int64_t m_given = 0) {
+  if (!(hp >= c->hmin)) FAIL(c, AQC_E_NUMERIC, "step size %.3e fell below the minimum %.3e", hp, c->hmin);
+  const double R = c->T - t0;
+  c->seg_m = m_given > 0 ? m_given : segment_steps(R, hp);
+  c->h = m_given > 0 ? c->T / (double)m_given : R / (double)c->seg_m;
+  c->seg_t0 = t0;
+  c->step = 0;
+  c->hist_ready = false;
+  c->small_run = 0;
+  c->seg_done0 = c->steps_done;
+  if (c->adaptive)  // kept until the segment's first PEC step is accepted
+    CUDA_TRY(c, cudaMemcpyAsync(c->vec_save, c->vec[V_Y], (size_t)c->N * c->amp, cudaMemcpyDeviceToDevice,
+                                c->stream));
+  aqc_segment sg;
+  memset(&sg, 0, sizeof(sg));
+  sg.t0 = t0;
+  sg.h = c->h;
+  sg.end = AQC_SEG_RUNNING;
+  c->segs.push_back(sg);
+  return AQC_OK;
+}
+
+// The first segment after an initial state: the grid of n_steps (or the step rule), h = T / N.
+int plan_first_segment(aqc_ctx* c) {
+  if (c->nsteps != 0) return AQC_OK;
+  c->nsteps = c->nsteps_req > 0 ? c->nsteps_req : rule_steps(c);
+  c->hmin = (c->T / (double)c->nsteps) * 0x1p-30;
+  c->segs.clear();
+  return begin_segment(c, 0.0, c->T / (double)c->nsteps, c->nsteps);
+}
+
+// One accepted grid step of the current segment.
+void count_step(aqc_ctx* c) {
   c->step++;
+  c->steps_done++;
+  c->segs.back().steps++;
+  if (c->step >= c->seg_m) {
+    c->at_end = true;
+    c->segs.back().end = AQC_SEG_AT_T;
+  }
+}
+
+// Step-size control after a PEC step whose y_{n+1} sits in the scratch vector: accept (the
+// scratch becomes y) if (19/270)||y_{n+1} - p_{n+1}|| <= tol ||y_{n+1}||, else restart from this
+// step's start with h/2; after grow_after small estimates in a row, restart with 2h.
+int control_step(aqc_ctx* c) {
+  double sl[kSlotCount];
+  CUDA_TRY(c, cudaMemcpyAsync(sl, c->d_slots, sizeof(sl), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const double e = sl[kSlotLastErr], y2 = sl[kSlotNorm2];
+  if (sl[kSlotFault] != 0.0) FAIL(c, AQC_E_TIMEOUT, "a kernel gave up waiting (a tile copy or a slab's partial sums)");
+  if (!std::isfinite(e) || !std::isfinite(y2)) FAIL(c, AQC_E_NUMERIC, "non-finite error estimate or norm");
+  const double lim = c->tol * sqrt(y2);
+  if (!(e <= lim)) {
+    c->rejects++;
+    c->segs.back().end = AQC_SEG_REJECTED;
+    if (c->step == 3) {  // the segment's first PEC step also judged its RK4 start-up: redo it all
+      std::swap(c->vec[V_Y], c->vec_save);
+      c->steps_done = c->seg_done0;
+      c->segs.back().steps = 0;
+      return begin_segment(c, c->seg_t0, 0.5 * c->h);
+    }
+    return begin_segment(c, c->seg_t0 + (double)c->step * c->h, 0.5 * c->h);
+  }
+  std::swap(c->vec[V_Y], c->vec[V_ACC]);
+  if (e > c->max_err_acc) c->max_err_acc = e;
+  count_step(c);
+  if (c->at_end) return AQC_OK;
+  c->small_run = e <= lim / 32.0 ? c->small_run + 1 : 0;
+  if (c->grow_after > 0 && c->small_run >= c->grow_after) {
+    c->segs.back().end = AQC_SEG_GREW;
+    return begin_segment(c, c->seg_t0 + (double)c->step * c->h, 2.0 * c->h);
+  }
   return AQC_OK;
 }
 
@@ -1028,11 +1131,14 @@ void release_transfers(aqc_ctx* c) {
 
 extern "C" {
 
-size_t aqc_workspace_bytes(int n_qubits, int precision) {
+size_t aqc_workspace_bytes_ex(int n_qubits, int precision, unsigned flags) {
   if (n_qubits < 1 || n_qubits > kMaxN) return 0;
   if (precision != AQC_C128 && precision != AQC_C64) return 0;
-  return plan_workspace(n_qubits, precision).total;
+  if (flags & ~(unsigned)AQC_WS_STEP_CONTROL) return 0;
+  return plan_workspace(n_qubits, precision, flags).total;
 }
+
+size_t aqc_workspace_bytes(int n_qubits, int precision) { return aqc_workspace_bytes_ex(n_qubits, precision, 0); }
 
 int aqc_create(aqc_ctx** out, int device, int precision, int n_qubits, void* workspace, size_t workspace_bytes,
                void* cuda_stream) {
@@ -1086,6 +1192,8 @@ int aqc_create(aqc_ctx** out, int device, int precision, int n_qubits, void* wor
   c->d_partials = (double*)(c->ws + wp.off_partials);
   c->d_dcode = (uint8_t*)(c->ws + wp.off_dcode);
   for (int v = 0; v < V_COUNT; v++) c->vec[v] = c->ws + wp.off_vec + (size_t)v * wp.vec_bytes;
+  if (workspace_bytes >= plan_workspace(n_qubits, precision, AQC_WS_STEP_CONTROL).total)
+    c->vec_save = c->ws + wp.off_vec + (size_t)V_COUNT * wp.vec_bytes;
   for (int g = 0; g < 3; g++)
     for (int k = 0; k < 4; k++) c->poly[g][k] = 0.0;
   DeviceGuard dg(device);
@@ -1211,13 +1319,28 @@ int aqc_set_slab_bits(aqc_ctx* ctx, int slab_bits) {
   return AQC_OK;
 }
 
-int aqc_set_integrator(aqc_ctx* ctx, int64_t n_steps, double kappa) {
+int aqc_set_integrator(aqc_ctx* ctx, int64_t n_steps, double kappa, int adaptive, double tol) {
   if (!ctx) return AQC_E_INVAL;
   if (n_steps < 0) FAIL(ctx, AQC_E_INVAL, "n_steps must be >= 0");
   if (kappa < 0.0 || !isfinite(kappa)) FAIL(ctx, AQC_E_INVAL, "kappa must be >= 0");
+  if (adaptive != 0 && adaptive != 1) FAIL(ctx, AQC_E_INVAL, "adaptive must be 0 or 1");
+  if (adaptive && !(tol > 0.0 && isfinite(tol))) FAIL(ctx, AQC_E_INVAL, "tol must be positive and finite");
+  if (adaptive && ctx->in_batch) FAIL(ctx, AQC_E_STATE, "a batch member cannot take step-size control");
+  if (adaptive && !ctx->vec_save)
+    FAIL(ctx, AQC_E_NOMEM, "the workspace has no room for step-size control (aqc_workspace_bytes_ex with "
+                           "AQC_WS_STEP_CONTROL)");
   ctx->nsteps_req = n_steps;
   ctx->kappa = kappa > 0.0 ? kappa : 0.1;
+  ctx->adaptive = adaptive;
+  ctx->tol = adaptive ? tol : 0.0;
   ctx->have_state = false;
+  return AQC_OK;
+}
+
+int aqc_set_step_growth(aqc_ctx* ctx, int grow_after) {
+  if (!ctx) return AQC_E_INVAL;
+  if (grow_after < 0) FAIL(ctx, AQC_E_INVAL, "grow_after must be >= 0");
+  ctx->grow_after = grow_after;
   return AQC_OK;
 }
 
@@ -1225,6 +1348,7 @@ int aqc_get_grid(aqc_ctx* ctx, int64_t* n_steps, double* h) {
   if (!ctx) return AQC_E_INVAL;
   if (!ctx->have_sched) FAIL(ctx, AQC_E_STATE, "no schedule set");
   const int64_t N = ctx->nsteps > 0 ? ctx->nsteps : (ctx->nsteps_req > 0 ? ctx->nsteps_req : rule_steps(ctx));
+  // (under step-size control: the initial grid, whose step the first segment takes)
   if (n_steps) *n_steps = N;
   if (h) *h = ctx->T / (double)N;
   return AQC_OK;
@@ -1296,6 +1420,13 @@ int aqc_set_initial_state(aqc_ctx* ctx, int kind, uint64_t basis, const void* us
   ctx->evals = 0;
   ctx->nsteps = 0;
   ctx->hist_ready = false;
+  ctx->steps_done = 0;
+  ctx->at_end = false;
+  ctx->rejects = 0;
+  ctx->max_err_acc = 0.0;
+  ctx->seg_t0 = 0.0;
+  ctx->seg_m = 0;
+  ctx->segs.clear();
   ctx->have_state = true;
   return AQC_OK;
 }
@@ -1306,11 +1437,9 @@ int aqc_propagate(aqc_ctx* ctx, int64_t max_steps, aqc_stats* stats) {
   DeviceGuard dg(ctx->device);
   int rc = ensure_ready(ctx);
   if (rc) return rc;
-  if (ctx->nsteps == 0) {
-    ctx->nsteps = ctx->nsteps_req > 0 ? ctx->nsteps_req : rule_steps(ctx);
-    ctx->h = ctx->T / (double)ctx->nsteps;
-  }
-  const int64_t target = max_steps < 0 ? ctx->nsteps : std::min(ctx->nsteps, ctx->step + max_steps);
+  rc = plan_first_segment(ctx);
+  if (rc) return rc;
+  const int64_t target = max_steps < 0 ? INT64_MAX : ctx->steps_done + max_steps;
   const int64_t launches0 = ctx->launches;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (stats) {
@@ -1318,15 +1447,22 @@ int aqc_propagate(aqc_ctx* ctx, int64_t max_steps, aqc_stats* stats) {
     CUDA_TRY(ctx, cudaEventCreate(&e1));
     CUDA_TRY(ctx, cudaEventRecord(e0, ctx->stream));
   }
-  while (ctx->step < target) {
+  while (!ctx->at_end && ctx->steps_done < target) {
     if (ctx->step < 3) {
       rc = rk4_step(ctx);
+      if (!rc) count_step(ctx);
     } else {
       if (!ctx->hist_ready) {
         rc = start_history(ctx);
         if (rc) break;
       }
       rc = pec_step(ctx);
+      if (!rc) {
+        if (ctx->adaptive)
+          rc = control_step(ctx);
+        else
+          count_step(ctx);
+      }
     }
     if (rc) break;
   }
@@ -1334,12 +1470,14 @@ int aqc_propagate(aqc_ctx* ctx, int64_t max_steps, aqc_stats* stats) {
     cudaEventRecord(e1, ctx->stream);
     if (!rc) {
       memset(stats, 0, sizeof(*stats));
-      stats->steps_done = ctx->step;
-      stats->n_steps = ctx->nsteps;
+      stats->steps_done = ctx->steps_done;
+      stats->n_steps = ctx->adaptive ? ctx->steps_done + (ctx->seg_m - ctx->step) : ctx->nsteps;
       stats->evaluations = ctx->evals;
       stats->h = ctx->h;
-      stats->t = (double)ctx->step * ctx->h;
+      stats->t = ctx->seg_t0 + (double)ctx->step * ctx->h;
       stats->launches = ctx->launches - launches0;
+      stats->rejects = ctx->rejects;
+      stats->segments = (int64_t)ctx->segs.size();
       cudaError_t e = launch_reduce(ctx->prec, 0, ctx->vec[V_Y], ctx->N, ctx->d_partials, ctx->d_counter,
                                     ctx->d_slots, reduce_grid(ctx->N), ctx->stream);
       ctx->launches++;
@@ -1354,12 +1492,12 @@ int aqc_propagate(aqc_ctx* ctx, int64_t max_steps, aqc_stats* stats) {
         rc = AQC_E_CUDA;
       } else {
         stats->norm2 = sl[kSlotNorm2];
-        stats->max_err_est = sl[kSlotMaxErr];
+        stats->max_err_est = ctx->adaptive ? ctx->max_err_acc : sl[kSlotMaxErr];
         stats->last_err_est = sl[kSlotLastErr];
         stats->elapsed_ms = ms;
         if (sl[kSlotFault] != 0.0) {
           ctx->err = "a kernel gave up waiting (a tile copy or a slab's partial sums); results are invalid";
-          rc = AQC_E_CUDA;
+          rc = AQC_E_TIMEOUT;
           const double zero = 0.0;
           cudaMemcpyAsync(ctx->d_slots + kSlotFault, &zero, sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
           cudaStreamSynchronize(ctx->stream);
@@ -1373,6 +1511,15 @@ int aqc_propagate(aqc_ctx* ctx, int64_t max_steps, aqc_stats* stats) {
     cudaEventDestroy(e1);
   }
   return rc;
+}
+
+int aqc_get_segments(aqc_ctx* ctx, aqc_segment* out, int64_t max_out, int64_t* count) {
+  if (!ctx) return AQC_E_INVAL;
+  if (max_out < 0 || (max_out > 0 && !out)) FAIL(ctx, AQC_E_INVAL, "out is NULL or max_out < 0");
+  const int64_t n = (int64_t)ctx->segs.size();
+  for (int64_t i = 0; i < n && i < max_out; i++) out[i] = ctx->segs[(size_t)i];
+  if (count) *count = n;
+  return AQC_OK;
 }
 
 int aqc_get_state(aqc_ctx* ctx, void* dst, int dst_on_device) {
@@ -1470,17 +1617,25 @@ int aqc_fidelity(aqc_ctx* ctx, uint64_t w, double* out) {
   return read_slot(ctx, kSlotDot, out);
 }
 
-int aqc_energy(aqc_ctx* ctx, int group, double* out) {
+int aqc_energy(aqc_ctx* ctx, int group_mask, double t, double* out) {
   if (!ctx || !out) return AQC_E_INVAL;
-  if (group < 0 || group > 2) FAIL(ctx, AQC_E_INVAL, "group must be 0, 1 or 2");
+  if (group_mask < 1 || group_mask > 7) FAIL(ctx, AQC_E_INVAL, "group_mask must be in 1..7");
+  if (!std::isfinite(t)) FAIL(ctx, AQC_E_INVAL, "t must be finite");
   DeviceGuard dg(ctx->device);
   if (ctx->dirty) {
     int rc = build_tables(ctx);
     if (rc) return rc;
   }
   double w[3] = {0.0, 0.0, 0.0};
-  w[group] = 1.0;
-  if (ctx->T > 0.0) ctx->eval_s = sched_s(ctx, (double)ctx->step * ctx->h);  // s at the current time
+  if (t >= 0.0) {
+    if (!ctx->have_sched) FAIL(ctx, AQC_E_STATE, "no schedule set");
+    sched_weights(ctx, t, w);  // also sets s(t) for a clause-by-clause sequence
+    for (int g = 0; g < 3; g++)
+      if (!((group_mask >> g) & 1)) w[g] = 0.0;
+  } else {
+    for (int g = 0; g < 3; g++) w[g] = ((group_mask >> g) & 1) ? 1.0 : 0.0;
+    if (ctx->T > 0.0) ctx->eval_s = sched_s(ctx, ctx->seg_t0 + (double)ctx->step * ctx->h);  // s now
+  }
   ApplyParams fin = base_params(ctx);
   fin.mode = MODE_ENERGY;
   int rc = evaluate(ctx, w, ctx->vec[V_Y], fin, nullptr);
@@ -1529,6 +1684,64 @@ double tridiag_eig(const double* a, const double* b, int k, int j) {
       lo = mid;
   }
   return 0.5 * (lo + hi);
+}
+
+// Eigenvector of the symmetric tridiagonal (a, b) for the eigenvalue lam: inverse iteration with
+// a row-pivoted LU of (T - lam I) (three sweeps from a fixed start), normalised, sign chosen so
+// that s[0] >= 0.
+void tridiag_eigvec(const double* a, const double* b, int k, double lam, double* s) {
+  if (k == 1) {
+    s[0] = 1.0;
+    return;
+  }
+  std::vector<double> dd(k), du(k, 0.0), du2(k, 0.0), mult(k, 0.0);
+  std::vector<char> piv(k, 0);
+  double scale = 0.0;
+  for (int i = 0; i < k; i++) scale = std::max(scale, fabs(a[i] - lam) + (i < k - 1 ? fabs(b[i]) : 0.0));
+  const double tiny = std::max(scale, 1e-300) * 1e-18;
+  for (int i = 0; i < k; i++) dd[i] = a[i] - lam;
+  for (int i = 0; i < k - 1; i++) du[i] = b[i];
+  for (int i = 0; i < k - 1; i++) {
+    const double dl = b[i];
+    if (fabs(dd[i]) >= fabs(dl)) {
+      if (dd[i] == 0.0) dd[i] = tiny;
+      mult[i] = dl / dd[i];
+      dd[i + 1] -= mult[i] * du[i];
+    } else {  // rows i and i+1 trade places
+      piv[i] = 1;
+      mult[i] = dd[i] / dl;
+      dd[i] = dl;
+      const double tmp = dd[i + 1];
+      dd[i + 1] = du[i] - mult[i] * tmp;
+      if (i < k - 2) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -mult[i] * du2[i];
+      }
+      du[i] = tmp;
+    }
+  }
+  if (dd[k - 1] == 0.0) dd[k - 1] = tiny;
+  for (int i = 0; i < k; i++) s[i] = 1.0 + 0.01 * (double)(i % 7);
+  for (int sweep = 0; sweep < 3; sweep++) {
+    for (int i = 0; i < k - 1; i++) {
+      if (!piv[i]) {
+        s[i + 1] -= mult[i] * s[i];
+      } else {
+        const double t = s[i];
+        s[i] = s[i + 1];
+        s[i + 1] = t - mult[i] * s[i];
+      }
+    }
+    s[k - 1] /= dd[k - 1];
+    s[k - 2] = (s[k - 2] - du[k - 2] * s[k - 1]) / dd[k - 2];
+    for (int i = k - 3; i >= 0; i--) s[i] = (s[i] - du[i] * s[i + 1] - du2[i] * s[i + 2]) / dd[i];
+    double nrm = 0.0;
+    for (int i = 0; i < k; i++) nrm += s[i] * s[i];
+    nrm = sqrt(nrm);
+    for (int i = 0; i < k; i++) s[i] /= nrm;
+  }
+  if (s[0] < 0.0)
+    for (int i = 0; i < k; i++) s[i] = -s[i];
 }
 
 struct LzPlan {
@@ -1663,6 +1876,7 @@ int aqc_batch_add(aqc_batch* b, aqc_ctx* c, int* slot_out) {
   if (!c->have_state) BFAIL(b, AQC_E_STATE, "context has no initial state");
   for (const ClauseH& k : c->clauses)
     if (k.stepwise) BFAIL(b, AQC_E_UNSUPPORTED, "clause-by-clause sequences are not batched");
+  if (c->adaptive) BFAIL(b, AQC_E_UNSUPPORTED, "contexts under step-size control are not batched");
   for (aqc_ctx* m : b->members)
     if (m == c) BFAIL(b, AQC_E_INVAL, "context is already a member");
   int slot = -1;
@@ -1683,16 +1897,21 @@ int aqc_batch_add(aqc_batch* b, aqc_ctx* c, int* slot_out) {
     c->dirty = true;
     BFAIL(b, rc, "member: %s", c->err.c_str());
   }
-  if (c->nsteps == 0) {
-    c->nsteps = c->nsteps_req > 0 ? c->nsteps_req : rule_steps(c);
-    c->h = c->T / (double)c->nsteps;
+  rc = plan_first_segment(c);
+  if (rc) {
+    c->in_batch = false;
+    c->dirty = true;
+    BFAIL(b, rc, "member: %s", c->err.c_str());
   }
   // start-up on the batch stream: RK4 steps, f_3 and the first predictor (after the
   // context's own queued work, e.g. its initial state)
   BCUDA(b, cudaStreamSynchronize(c->stream));
   cudaStream_t saved = c->stream;
   c->stream = b->stream;
-  while (rc == 0 && c->step < 3 && c->step < c->nsteps) rc = rk4_step(c);
+  while (rc == 0 && c->step < 3 && c->step < c->nsteps) {
+    rc = rk4_step(c);
+    if (!rc) count_step(c);
+  }
   if (rc == 0 && c->step >= 3 && c->step < c->nsteps && !c->hist_ready) rc = start_history(c);
   c->stream = saved;
   if (rc) BFAIL(b, rc, "member start-up: %s", c->err.c_str());
@@ -1718,6 +1937,12 @@ int aqc_batch_remove(aqc_batch* b, int slot) {
   const BatchInst& I = b->h_insts[slot];
   c->evals += I.step - b->step_at_add[slot];
   c->step = I.step;
+  c->steps_done = I.step;  // one segment from t = 0 (batch members run the fixed-step grid)
+  if (!c->segs.empty()) c->segs.back().steps = I.step;
+  if (c->step >= c->seg_m) {
+    c->at_end = true;
+    if (!c->segs.empty()) c->segs.back().end = AQC_SEG_AT_T;
+  }
   if (c->step >= 3) c->hist_ready = true;
   // carry the member's reductions into the context's result slots
   double sl[3] = {I.norm2, I.max_err, I.last_err};
@@ -1793,6 +2018,12 @@ size_t aqc_lanczos_workspace_bytes(int n_qubits, int precision, int max_iter) {
       max_iter > 4096)
     return 0;
   return lanczos_plan(n_qubits, precision, max_iter).total;
+}
+
+int aqc_tridiag_eigvec(int k, const double* a, const double* b, double lam, double* out) {
+  if (k < 1 || !a || (k > 1 && !b) || !out || !std::isfinite(lam)) return AQC_E_INVAL;
+  tridiag_eigvec(a, b, k, lam, out);
+  return AQC_OK;
 }
 
 int aqc_tridiag_eigvals(int k, const double* a, const double* b, int n_eig, double* out) {
@@ -1887,6 +2118,117 @@ int aqc_lanczos(aqc_ctx* ctx, double t, const void* start, void* work, size_t wo
     eig[e] = e < m ? tridiag_eig(alpha.data(), beta.data(), iters, e) : NAN;
     if (conv) conv[e] = e < m ? chg[e] : NAN;
   }
+  if (iters_out) *iters_out = iters;
+  return AQC_OK;
+}
+
+int aqc_lanczos_ground(aqc_ctx* ctx, double t, const void* start, void* work, size_t work_bytes, int max_iter,
+                       double tol, double* theta_out, double* resid_out, void* ground_out, int* iters_out) {
+  if (!ctx) return AQC_E_INVAL;
+  if (!start || !work || !theta_out || !ground_out) FAIL(ctx, AQC_E_INVAL, "start, work, theta and ground_out must be non-NULL");
+  if (max_iter < 1 || max_iter > 4096 || !(tol >= 0.0)) FAIL(ctx, AQC_E_INVAL, "need 1 <= max_iter <= 4096 and tol >= 0");
+  const LzPlan P = lanczos_plan(ctx->n, ctx->prec, max_iter);
+  if (work_bytes < P.total) FAIL(ctx, AQC_E_NOMEM, "work has %zu bytes, %zu needed", work_bytes, P.total);
+  if (((uintptr_t)work & 255u) || ((uintptr_t)start & 15u) || ((uintptr_t)ground_out & 15u))
+    FAIL(ctx, AQC_E_INVAL, "work must be 256-byte aligned, start and ground_out 16-byte aligned");
+  if (!ctx->have_sched) FAIL(ctx, AQC_E_STATE, "no schedule set");
+  DeviceGuard dg(ctx->device);
+  if (ctx->dirty) {
+    int rc = build_tables(ctx);
+    if (rc) return rc;
+  }
+  double w[3];
+  sched_weights(ctx, t, w);
+  char* base = (char*)work;
+  const uint64_t ld = P.ld_bytes / ctx->amp;
+  auto V = [&](int i) { return (void*)(base + (size_t)i * P.ld_bytes); };
+  double* partials = (double*)(base + P.off_partials);
+  double* coef = (double*)(base + P.off_coef);
+  double* h = (double*)(base + P.off_h);
+  double* scal = (double*)(base + P.off_scal);
+  cudaStream_t s = ctx->stream;
+  const uint64_t N = ctx->N;
+  const size_t bytes = (size_t)N * ctx->amp;
+  if (ctx->permuted) {
+    int rc = to_library_order(ctx, V(0), start);
+    if (rc) return rc;
+  } else {
+    CUDA_TRY(ctx, cudaMemcpyAsync(V(0), start, bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  CUDA_TRY(ctx, launch_dotc_multi(ctx->prec, V(0), ld, 1, V(0), N, partials, scal, nullptr, s));
+  CUDA_TRY(ctx, launch_scale_to(ctx->prec, V(0), V(0), N, scal, s));
+  ctx->launches += 3;
+  std::vector<double> alpha, beta, sv;
+  int iters = 0;
+  double theta = 0.0;
+  for (int j = 0; j < max_iter; j++) {
+    void* wv = V(j + 1);
+    ApplyParams fin = base_params(ctx);
+    fin.mode = MODE_PARTIAL;
+    int rc = evaluate(ctx, w, V(j), fin, wv);
+    if (rc) return rc;
+    CUDA_TRY(ctx, cudaMemsetAsync(h, 0, (size_t)(j + 1) * 2 * sizeof(double), s));
+    for (int pass = 0; pass < 2; pass++) {  // classical Gram-Schmidt, twice
+      CUDA_TRY(ctx, launch_dotc_multi(ctx->prec, V(0), ld, (uint32_t)(j + 1), wv, N, partials, coef, h, s));
+      CUDA_TRY(ctx, launch_sub_multi(ctx->prec, wv, V(0), ld, (uint32_t)(j + 1), coef, N, s));
+      ctx->launches += 3;
+    }
+    CUDA_TRY(ctx, launch_dotc_multi(ctx->prec, wv, ld, 1, wv, N, partials, scal, nullptr, s));
+    ctx->launches += 2;
+    double hj[2], nrm2[2];
+    CUDA_TRY(ctx, cudaMemcpyAsync(hj, h + 2 * j, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaMemcpyAsync(nrm2, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (!std::isfinite(hj[0]) || !std::isfinite(nrm2[0])) FAIL(ctx, AQC_E_NUMERIC, "non-finite Lanczos coefficient");
+    alpha.push_back(hj[0]);
+    const double bj = sqrt(std::max(nrm2[0], 0.0));
+    iters = j + 1;
+    const bool invariant = bj <= 1e-13 * std::max(1.0, fabs(hj[0]));
+    if (invariant || iters == max_iter || iters % 4 == 0) {
+      // Ritz residual of the lowest pair: ||H x - theta x|| = beta_j |s_last|
+      theta = tridiag_eig(alpha.data(), beta.data(), iters, 0);
+      sv.assign(iters, 0.0);
+      tridiag_eigvec(alpha.data(), beta.data(), iters, theta, sv.data());
+      if (invariant || bj * fabs(sv[iters - 1]) <= tol * std::max(1.0, fabs(theta)) || iters == max_iter) break;
+    }
+    beta.push_back(bj);
+    CUDA_TRY(ctx, launch_scale_to(ctx->prec, wv, wv, N, scal, s));
+    ctx->launches++;
+  }
+  // x = sum_i s_i v_i into V(iters) (free: the last, unnormalised residual), then unit norm
+  void* x = V(iters);
+  std::vector<double> c(2 * (size_t)iters, 0.0);
+  for (int i = 0; i < iters; i++) c[2 * (size_t)i] = -sv[i];
+  CUDA_TRY(ctx, cudaMemcpyAsync(coef, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(ctx, cudaMemsetAsync(x, 0, bytes, s));
+  CUDA_TRY(ctx, launch_sub_multi(ctx->prec, x, V(0), ld, (uint32_t)iters, coef, N, s));
+  CUDA_TRY(ctx, launch_dotc_multi(ctx->prec, x, ld, 1, x, N, partials, scal, nullptr, s));
+  CUDA_TRY(ctx, launch_scale_to(ctx->prec, x, x, N, scal, s));
+  ctx->launches += 4;
+  // residual ||H x - theta x|| with one more matvec (into the scratch vector)
+  {
+    ApplyParams fin = base_params(ctx);
+    fin.mode = MODE_PARTIAL;
+    int rc = evaluate(ctx, w, x, fin, ctx->vec[V_ACC]);
+    if (rc) return rc;
+    const double th[2] = {theta, 0.0};
+    CUDA_TRY(ctx, cudaMemcpyAsync(coef, th, sizeof(th), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(ctx, launch_sub_multi(ctx->prec, ctx->vec[V_ACC], x, ld, 1, coef, N, s));
+    CUDA_TRY(ctx, launch_dotc_multi(ctx->prec, ctx->vec[V_ACC], ld, 1, ctx->vec[V_ACC], N, partials, scal, nullptr, s));
+    ctx->launches += 3;
+    double r2[2];
+    CUDA_TRY(ctx, cudaMemcpyAsync(r2, scal, sizeof(r2), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (resid_out) *resid_out = sqrt(std::max(r2[0], 0.0));
+  }
+  if (ctx->permuted) {
+    int rc = to_qubit_order(ctx, ground_out, x);
+    if (rc) return rc;
+  } else {
+    CUDA_TRY(ctx, cudaMemcpyAsync(ground_out, x, bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  *theta_out = theta;
   if (iters_out) *iters_out = iters;
   return AQC_OK;
 }

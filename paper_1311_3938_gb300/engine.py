@@ -24,7 +24,9 @@ def _torch_dtype(precision):
 class Context:
     """One state vector of n qubits on one GPU with its integrator (include/aqc.h)."""
 
-    def __init__(self, n: int, precision: int = N.AQC_C128, device: int = 0, stream=None):
+    def __init__(self, n: int, precision: int = N.AQC_C128, device: int = 0, stream=None, step_control=False):
+        """step_control=True reserves the workspace vector that step-size control needs
+        (set_integrator(adaptive=True))."""
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
         self.n = n
@@ -32,7 +34,7 @@ class Context:
         self.device = device
         self.dev = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
-        self.ws_bytes = N.aqc_workspace_bytes(n, precision)
+        self.ws_bytes = N.aqc_workspace_bytes_ex(n, precision, N.AQC_WS_STEP_CONTROL if step_control else 0)
         if self.ws_bytes == 0:
             raise ValueError("unsupported n / precision")
         # +256 so that the pointer can be aligned
@@ -103,8 +105,17 @@ class Context:
         """Slab order of the PEC step: 0 off, -1 automatic, k > 0 at most k slab bits."""
         N.aqc_set_slab_bits(self.handle, slab_bits)
 
-    def set_integrator(self, n_steps=0, kappa=0.0):
-        N.aqc_set_integrator(self.handle, n_steps, kappa)
+    def set_integrator(self, n_steps=0, kappa=0.0, adaptive=False, tol=0.0):
+        """Fixed-step grid (n_steps, or the step rule with kappa), or step-size control with a
+        relative tolerance tol per PEC step (adaptive=True; aqc.h, aqc_set_integrator)."""
+        N.aqc_set_integrator(self.handle, n_steps, kappa, 1 if adaptive else 0, tol)
+
+    def set_step_growth(self, grow_after=16):
+        N.aqc_set_step_growth(self.handle, grow_after)
+
+    def segments(self):
+        """[(t0, h, accepted steps, end)] of the run's segments of constant step."""
+        return N.aqc_get_segments(self.handle)
 
     def set_initial_state(self, state="uniform"):
         """"uniform" (|S>), a basis index, ("dicke", k) (Eq. initstate), "staged" (the vector of
@@ -192,7 +203,15 @@ class Context:
         return N.aqc_fidelity(self.handle, w)
 
     def energy(self, group=N.AQC_GRP_B):
-        return N.aqc_energy(self.handle, group)
+        """<psi|H_group|psi> with unit weight (the final energy of Sec. II.B for group B)."""
+        return N.aqc_energy(self.handle, 1 << group, N.AQC_UNIT_WEIGHTS)
+
+    def energy_at(self, t, groups=(N.AQC_GRP_A, N.AQC_GRP_B, N.AQC_GRP_C)):
+        """<psi| sum_{g in groups} w_g(s(t)) H_g |psi> (all groups: <H(t)>)."""
+        mask = 0
+        for g in groups:
+            mask |= 1 << g
+        return N.aqc_energy(self.handle, mask, float(t))
 
     def norm2(self):
         return N.aqc_norm2(self.handle)
@@ -211,6 +230,20 @@ class Context:
             out = N.aqc_lanczos(self.handle, t, start.data_ptr(), work.data_ptr() + off, nbytes, max_iter, n_eig, tol)
             del work, start
         return out
+
+    def lanczos_ground(self, t, start: torch.Tensor, max_iter=300, tol=1e-12):
+        """Lowest eigenpair of H(t) reachable from `start` (aqc_lanczos_ground): returns
+        (device vector x, theta, residual ||H x - theta x||, iterations)."""
+        nbytes = N.aqc_lanczos_workspace_bytes(self.n, self.precision, max_iter)
+        with torch.cuda.stream(self.stream):
+            start = start.to(self.dev, _torch_dtype(self.precision)).contiguous()
+            work = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.dev)
+            off = (-work.data_ptr()) % 256
+            x = torch.empty(self.N, dtype=_torch_dtype(self.precision), device=self.dev)
+            theta, resid, iters = N.aqc_lanczos_ground(self.handle, t, start.data_ptr(), work.data_ptr() + off, nbytes,
+                                                       max_iter, tol, x.data_ptr())
+            del work, start
+        return x, theta, resid, iters
 
     def hpsi(self, t, psi: torch.Tensor, out: torch.Tensor = None):
         """out = H(t) psi for device tensors of the state dtype."""
