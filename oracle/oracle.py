@@ -11,6 +11,8 @@ Contents
       H^xyz = Omega sum_{i<j} n_ij/2 (1 - sigma_i . sigma_j)  (Eq. Hixyz)
       H^xy  = 3 m Omega 1 - Omega sum_{i<j} n_ij/2 (X_i X_j + Y_i Y_j)   (Eq. Hixy)
   * `dicke_state`: the balanced superposition over one Hamming weight (Eq. initstate).
+  * `xy_sector_ground_state`: the ground state of H^xy in one Hamming-weight sector (the XY
+    algorithm's start, Sec. III.A.3), by dense diagonalisation of the sector block.
   * `hpsi` / `propagate`: thin ctypes calls into aqc_oracle.c (scatter-form SQH matvec, RK4
     start-up + Adams-Bashforth-Moulton-4 PEC integrator).
   * `dense_matrix`: explicit 2x2 Pauli matrices combined with Kronecker products, qubit 1 as
@@ -263,6 +265,33 @@ def dicke_state(n, k):
     psi = np.zeros(N, dtype=np.complex128)
     psi[w == k] = 1.0 / math.sqrt(math.comb(n, k))
     return psi
+
+
+def xy_sector_ground_state(n, clauses, k, omega=1.0):
+    """Sec. III.A.3: the ground state of H^xy (Eq. Hixy) inside the sector of Hamming weight k
+    (Eq. Sigmaz), the start of the XY algorithm.  The sector block <u|H^xy|v> (|u| = |v| = k) is
+    built column by column from the oracle's matvec, diagonalised densely (numpy eigh), and the
+    lowest eigenvector embedded in the 2^n space with the sign fixed so that its amplitudes sum
+    to a non-negative number.  Returns (energy, state).  Sizes up to C(n, k) of a few thousand."""
+    H = Hamiltonian(n)
+    add_xy_driver(H, clauses, 0, omega)
+    w = [1.0, 0.0, 0.0, 0.0]
+    idx = np.array([z for z in range(1 << n) if bin(z).count("1") == k], dtype=np.int64)
+    if idx.size == 0:
+        raise ValueError("empty sector")
+    block = np.empty((idx.size, idx.size), dtype=np.complex128)
+    e = np.zeros(1 << n, dtype=np.complex128)
+    for c, z in enumerate(idx):
+        e[z] = 1.0
+        block[:, c] = hpsi(H, w, e)[idx]
+        e[z] = 0.0
+    lam, V = np.linalg.eigh(block)
+    v = V[:, 0]
+    if v.sum().real < 0:
+        v = -v
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[idx] = v
+    return float(lam[0]), psi
 
 
 def xy_hamiltonian(inst, driver="xy", penalty=PEN_INDICATOR, catalyst=None):

@@ -11,6 +11,10 @@
   outside the start sector exactly zero.
 * The XYZ algorithm started in the Dicke state of the solution's weight reaches the solution
   at large T, with the energy bound of Sec. II.B.
+* The XY algorithm's start, the ground state of H^xy in the solution's sector
+  (xy_sector_ground_state): against the sector block written from the hopping picture
+  (sigma+ sigma- moves), the closed form of the complete clause graph (total spin: the Dicke
+  state is the ground state, energy in closed form), and the Kronecker-product matrix.
 """
 import math
 
@@ -130,3 +134,84 @@ def test_xy_catalyst_path_matches_library_ode_solver():
     errs = [np.linalg.norm(O.propagate(H, sched, j * N, psi0).psi - ref) for j in (1, 2)]
     assert errs[0] < 2e-6
     assert 10.0 < errs[0] / errs[1] < 24.0
+
+
+# ---- the XY algorithm's start: ground state of H^xy in one Hamming-weight sector (Sec. III.A.3)
+
+
+def _hopping_block(n, clauses, k):
+    """The sector block of Eq. Hixy written from the hopping picture, without Pauli products:
+    (X_i X_j + Y_i Y_j)/2 = sigma+_i sigma-_j + sigma-_i sigma+_j moves a one-bit between i and
+    j, so <z'|H^xy|z> = -n_ij when z' is z with differing bits i, j swapped, and 3 m on the
+    diagonal."""
+    idx = [z for z in range(1 << n) if bin(z).count("1") == k]
+    pos = {z: a for a, z in enumerate(idx)}
+    nij = {}
+    for c in clauses:
+        for a in c:
+            for b in c:
+                if a < b:
+                    nij[(a, b)] = nij.get((a, b), 0) + 1
+    B = np.zeros((len(idx), len(idx)))
+    for a, z in enumerate(idx):
+        B[a, a] = 3.0 * len(clauses)
+        for (i, j), v in nij.items():
+            if ((z >> i) & 1) != ((z >> j) & 1):
+                B[pos[_swap(z, i, j)], a] -= v
+    return np.array(idx), B
+
+
+@pytest.mark.parametrize("n,seed", [(8, 1), (10, 2), (11, 4)])
+def test_xy_ground_state_against_the_hopping_block(n, seed):
+    """Energy and vector against the eigenpair of the hopping-picture block; the state lies in
+    the sector, has unit norm and (Perron-Frobenius: the block's off-diagonal entries are <= 0
+    on a connected clause graph) strictly positive amplitudes there."""
+    inst = generate_ec3(n, seed)
+    k = bin(inst.solution).count("1")
+    E, psi = O.xy_sector_ground_state(n, inst.clauses, k)
+    idx, B = _hopping_block(n, inst.clauses, k)
+    lam, V = np.linalg.eigh(B)
+    assert lam[1] - lam[0] > 1e-3  # unique ground state
+    v = V[:, 0] * np.sign(V[:, 0].sum())
+    assert abs(E - lam[0]) < 1e-11 * max(1.0, abs(lam[0]))
+    assert np.max(np.abs(psi[idx] - v)) < 1e-10
+    out = np.ones(1 << n, dtype=bool)
+    out[idx] = False
+    assert np.all(psi[out] == 0)
+    assert abs(np.vdot(psi, psi).real - 1.0) < 1e-13
+    assert np.all(psi[idx].real > 0) and np.max(np.abs(psi[idx].imag)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [4, 5, 6])
+def test_xy_ground_state_on_the_complete_graph_is_dicke(n):
+    """All C(n,3) triples as clauses: every pair has n_ij = n - 2, and with S = sum sigma / 2,
+    sum_{i<j} (X_i X_j + Y_i Y_j) = 2 (S^2 - S_z^2) - n.  The ground state of each sector is then
+    the Dicke state (total spin n/2), at energy 3 m - (n - 2)/2 [2 (n/2 (n/2 + 1) - (n/2 - k)^2) - n]."""
+    import itertools
+
+    clauses = [tuple(c) for c in itertools.combinations(range(n), 3)]
+    m = len(clauses)
+    for k in range(n + 1):
+        E, psi = O.xy_sector_ground_state(n, clauses, k)
+        want = 3.0 * m - (n - 2) / 2.0 * (2.0 * (n / 2 * (n / 2 + 1) - (n / 2 - k) ** 2) - n)
+        assert abs(E - want) < 1e-11 * max(1.0, abs(want)), (n, k, E, want)
+        assert np.max(np.abs(psi - O.dicke_state(n, k))) < 1e-12
+
+
+def test_xy_ground_state_against_the_kronecker_matrix():
+    """The dense 2^n matrix of Eq. Hixy built from Kronecker products (dense_matrix, its own
+    pins in test_oracle_pins.py): its lowest eigenvalue in the sector equals the energy, and
+    the state is an eigenvector of it to rounding."""
+    inst = generate_ec3(9, 6)
+    n, k = inst.n, bin(inst.solution).count("1")
+    E, psi = O.xy_sector_ground_state(n, inst.clauses, k)
+    H = O.Hamiltonian(n)
+    O.add_xy_driver(H, inst.clauses, 0)
+    D = O.dense_matrix(H, [1.0, 0.0, 0.0, 0.0])
+    idx = [z for z in range(1 << n) if bin(z).count("1") == k]
+    ev = np.linalg.eigvalsh(D[np.ix_(idx, idx)])
+    assert abs(ev[0] - E) < 1e-11 * max(1.0, abs(E))
+    assert np.linalg.norm(D @ psi - E * psi) < 1e-10
+    # below the Dicke state's energy (it is not an eigenstate of H^xy on this graph)
+    d = O.dicke_state(n, k)
+    assert E < np.vdot(d, D @ d).real - 1e-6
