@@ -1,14 +1,21 @@
 #!/usr/bin/env python3
 """Benchmark of the adiabatic-evolution hot path on one GB300 (or N replicas).
 
-Workload (one bench step = one pass of the whole hot path over one synthetic instance):
+Headline (one bench step = one pass of the whole hot path over one synthetic instance):
   Exact-Cover-3 instance, n = 28 qubits, seed 3; linear path H = (1-s) H_i + s H_f,
   s = t/T, T = 100; uniform start |S>; fixed-step grid from the step rule (kappa = 0.1).
   Each step: set psi(0) -> 3 RK4 start-up steps -> PEC steps (one fused H*psi per step) up to
   `--pec` grid steps -> P_1 and E(T-window) readback.  State in complex64 (headline) and
-  complex128 (reported beside it).
+  complex128 (reported beside it, against the FP64 FMA rate measured in the same run).
 Metric: H*psi GB/s = algorithmic bytes of the hot path / device time (inputs resident in HBM),
 with the fused PEC step's achieved bandwidth against the measured HBM copy peak.
+
+Beside it on the same line: the small-state workload (n = 10, T = 20: wall time per solve,
+step by step and with CUDA-graph replays), the batched workload (512 instances, n 12-22,
+T 10-200, with a one-at-a-time sample), the served request stream (n 10-26 and n = 30,
+T 10-500, under a stated time cap, and the same requests one at a time), the XY algorithm's
+PEC step, and per-result checks of the complex64 results with n <= 14 against the FP64
+oracle (spawned host processes running beside the GPU legs, outside every timed region).
 """
 from __future__ import annotations
 
@@ -48,9 +55,17 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-xy", action="store_true")
-    ap.add_argument("--batch-count", type=int, default=48)
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-count", type=int, default=40)
-    return ap.parse_args()
+    ap.add_argument("--serve-rate", type=float, default=1.0, help="requests per second (Poisson)")
+    ap.add_argument("--serve-cap", type=float, default=120.0, help="time cap of the served stream (s)")
+    ap.add_argument("--quick", action="store_true", help="small batched/served legs (not the stated workloads)")
+    a = ap.parse_args()
+    if a.quick:
+        a.batch_count, a.serve_count, a.serve_cap = 48, 16, 30.0
+    return a
 
 
 # ----------------------------------------------------------------------------- accounting
@@ -211,41 +226,237 @@ def cpu_sample(target_s=15.0):
     return gbs, cores, desc, dt
 
 
-# ----------------------------------------------------------------------------- batch / serve
-def measure_batched(a):
-    """Batched vs one-at-a-time solves on a sample of the 512-instance batched workload
-    (seeds from 1000, n ~ U{12..18}, nonlinear path, T ~ U[10, 40], complex64): same step
-    grids, so equal final-fidelity accuracy by construction (checked)."""
+# ----------------------------------------------------------------------------- oracle checks
+ORACLE_MAX_N = 14  # results checked against the FP64 oracle (host processes, outside timed regions)
+
+
+def _nice_worker():
+    try:
+        os.nice(10)  # below the bench's own host thread, which drives the GPU
+    except OSError:
+        pass
+
+
+def oracle_solve(spec):
+    """The FP64 CPU oracle on one job (X algorithm, EC3 instance of `seed`, uniform start), in
+    a spawned host process: returns (spec, grid steps, P_1, final state)."""
+    from instances import generate_ec3, xx_pairs
+    from oracle import oracle as O
+
+    n, seed, nonlinear, T, s_kind = spec["n"], spec["seed"], spec["nonlinear"], spec["T"], spec["s_kind"]
+    inst = generate_ec3(n, seed)
+    H = O.ec3_hamiltonian(inst, pairs=xx_pairs(n, seed) if nonlinear else None)
+    sched = (O.nonlinear_path if nonlinear else O.linear_path)(T, s_kind)
+    N = O.step_count(H, sched)
+    r = O.propagate(H, sched, N, O.uniform_state(n))
+    return spec, N, O.fidelity(r.psi, inst.solution), r.psi
+
+
+class OracleChecks:
+    """FP64 oracle solves of the checked jobs on the host cores (spawned processes, niced),
+    running while the GPU legs run; `results(timeout)` collects what finished."""
+
+    def __init__(self, workers):
+        import multiprocessing as mp
+
+        self.pool = mp.get_context("spawn").Pool(processes=workers, initializer=_nice_worker)
+        self.workers = workers
+        self.pending = {}
+
+    @staticmethod
+    def spec_of(job):
+        return {"n": job.n, "seed": job.seed, "nonlinear": bool(job.nonlinear), "T": float(job.T),
+                "s_kind": int(job.s_kind)}
+
+    def submit(self, key, spec):
+        self.pending[key] = self.pool.apply_async(oracle_solve, (spec,))
+
+    def results(self, timeout):
+        t_end = time.perf_counter() + timeout
+        out = {}
+        for key, r in self.pending.items():
+            try:
+                out[key] = r.get(timeout=max(0.0, t_end - time.perf_counter()))
+            except Exception:
+                pass
+        self.pool.terminate()
+        self.pool.join()
+        return out
+
+
+def oracle_errors(jobs, tag, oracle_results, max_n=ORACLE_MAX_N):
+    """Per-result comparison of finished complex64 jobs with n <= max_n against the oracle:
+    relative state error, |P_1 - P_1(oracle)|, equal step grids."""
+    import numpy as np
+
+    rows = []
+    for job in jobs:
+        if job.n > max_n or job.state is None:
+            continue
+        got = oracle_results.get((tag, job.jid))
+        if got is None:
+            continue
+        spec, N, P1_or, psi_or = got
+        a = job.state.astype(np.complex128)
+        rows.append({"n": job.n, "grid_steps": int(job.steps), "oracle_steps": int(N),
+                     "state_err": float(np.linalg.norm(a - psi_or) / np.linalg.norm(psi_or)),
+                     "P1_err": abs(job.P1 - P1_or)})
+    eligible = sum(1 for j in jobs if j.n <= max_n and j.state is not None)
+    return {
+        "checked": len(rows),
+        "eligible": eligible,
+        "max_n": max_n,
+        "max_state_err_vs_oracle": max((r["state_err"] for r in rows), default=None),
+        "max_P1_err_vs_oracle": max((r["P1_err"] for r in rows), default=None),
+        "step_grids_equal": all(r["grid_steps"] == r["oracle_steps"] for r in rows),
+        "state_bar": 1e-5,
+    }
+
+
+def quantile_censored(values, q):
+    """Nearest-rank quantile of latencies where unfinished requests count as +inf; returns
+    (value or None if it falls on an unfinished request, censored flag)."""
+    v = sorted(values)
+    if not v:
+        return None, False
+    k = max(0, math.ceil(q * len(v)) - 1)
+    return (None, True) if math.isinf(v[k]) else (v[k], False)
+
+
+# ----------------------------------------------------------------------------- workloads
+def batched_jobs(count):
+    from paper_1311_3938_gb300 import workloads as W
+
+    return W.random_jobs(count, 1000, n_range=(12, 22), T_range=(10.0, 200.0), nonlinear=True)
+
+
+def served_jobs(count, rate):
+    from paper_1311_3938_gb300 import workloads as W
+
+    return W.random_jobs(count, 2000, n_range=(10, 26), T_range=(10.0, 500.0), rate=rate, big_every=20, big_n=30,
+                         path_mix=True)
+
+
+def measure_batched(a, checks):
+    """The batched workload: `count` seeded EC3 instances (seeds from 1000), n ~ U{12..22},
+    nonlinear path, T ~ U[10, 200], complex64, all as members of one batch (autotuned shape).
+    One-at-a-time solves of all of them would take about 2x the batch time, so every 16th job
+    runs one at a time and batched again, for a like-for-like speedup at equal step grids."""
     import copy
 
     from paper_1311_3938_gb300 import autotune as A
     from paper_1311_3938_gb300 import workloads as W
 
-    jobs = W.random_jobs(a.batch_count, 1000, n_range=(12, 18), T_range=(10.0, 40.0), nonlinear=True)
-    shape, tune = A.autotune(jobs[: min(16, len(jobs))], rounds=3)
+    jobs = batched_jobs(a.batch_count)
+    for j in jobs:
+        j.keep = j.n <= ORACLE_MAX_N
+    shape, _ = A.autotune(copy.deepcopy(jobs[: min(16, len(jobs))]), rounds=3)
     tile_bits, threads, spr = shape
-    jb = copy.deepcopy(jobs)
-    t_batch = W.run_batched(jb, threads=threads, steps_per_round=spr, tile_bits=tile_bits)
-    js = copy.deepcopy(jobs)
-    t_seq = W.run_sequential(js)
-    dP1 = max(abs(x.P1 - y.P1) for x, y in zip(jb, js))
-    steps = sum(j.steps for j in jb)
+    t_batch = W.run_batched(jobs, threads=threads, steps_per_round=spr, tile_bits=tile_bits)
+    every = 16 if len(jobs) >= 64 else 1
+    sample = [copy.deepcopy(j) for j in jobs[::every]]
+    for j in sample:
+        j.keep, j.state = False, None
+    sb = copy.deepcopy(sample)
+    t_sb = W.run_batched(sb, threads=threads, steps_per_round=spr, tile_bits=tile_bits)
+    t_seq = W.run_sequential(sample)
+    dP1 = max(abs(x.P1 - y.P1) for x, y in zip(sb, sample))
+    steps = sum(j.steps for j in jobs)
+    amp_steps = sum(j.steps * (1 << j.n) for j in jobs)
     return {
-        "workload": f"{len(jobs)} EC3 instances, seeds 1000-{999 + len(jobs)}, n~U{{12..18}}, nonlinear, "
-                    "T~U[10,40], complex64 (sample of the 512-instance n~U{12..22} T~U[10,200] workload)",
+        "workload": f"{len(jobs)} EC3 instances, seeds 1000-{999 + len(jobs)}, n~U{{12..22}}, nonlinear path, "
+                    "T~U[10,200], complex64 (FP64 reductions), one batch, persistent k_batch under CUDA graphs",
+        "count": len(jobs),
+        "wall_s": t_batch,
         "solves_per_s_batched": len(jobs) / t_batch,
-        "solves_per_s_sequential": len(jobs) / t_seq,
-        "speedup": t_seq / t_batch,
         "grid_steps_total": steps,
+        "alg_GBs": 7 * 8 * amp_steps / t_batch / 1e9,
+        "sequential_sample": f"every {every}th job ({len(sample)} jobs) one at a time and batched again",
+        "solves_per_s_sequential": len(sample) / t_seq,
+        "sample_solves_per_s_batched": len(sample) / t_sb,
+        "sample_speedup": t_seq / t_sb,
         "max_abs_dP1_batched_vs_sequential": dP1,
         "autotuned_shape": {"tile_bits": tile_bits, "threads": threads, "steps_per_round": spr},
+        "_jobs": jobs,
+    }
+
+
+def measure_serving(a):
+    """The serving stream: `count` requests, Poisson arrivals at `rate`/s, n ~ U{10..26} with
+    every 20th request n = 30, path linear/nonlinear uniform, T ~ U[10, 500], complex64;
+    continuous batching (n <= 20 in the batch, larger states on their own streams) under the
+    HBM budget, ended at the time cap (requests then unfinished are censored).  The same
+    requests then run one at a time under the same cap."""
+    import copy
+
+    from paper_1311_3938_gb300 import workloads as W
+
+    jobs = served_jobs(a.serve_count, a.serve_rate)
+    for j in jobs:
+        j.keep = j.n <= ORACLE_MAX_N
+    seq_jobs = copy.deepcopy(jobs)
+    for j in seq_jobs:
+        j.keep = False
+    srv = W.Server(batch_max_n=20, max_members=128, steps_per_round=16, big_chunk=32)
+    try:
+        res = srv.serve(jobs, time_limit=a.serve_cap)
+    finally:
+        srv.close()
+    done = res.pop("jobs")
+    cens = res.pop("censored_jobs")
+    res.pop("not_admitted")
+    offered = [j for j in jobs if j.arrival <= a.serve_cap]
+    lat = [j.latency if not math.isnan(j.finished) else math.inf for j in offered]
+    p50, c50 = quantile_censored(lat, 0.50)
+    p99, c99 = quantile_censored(lat, 0.99)
+    s_done, s_cens, s_wall = W.serve_one_at_a_time(seq_jobs, time_limit=a.serve_cap)
+    s_lat = [j.latency if not math.isnan(j.finished) else math.inf for j in seq_jobs if j.arrival <= a.serve_cap]
+    sp50, sc50 = quantile_censored(s_lat, 0.50)
+    sp99, sc99 = quantile_censored(s_lat, 0.99)
+    # the n = 15..20 results against the library's own complex128 path (the oracle takes the n <= 14 ones)
+    W.attach_c128_errors(done, min_n=ORACLE_MAX_N + 1, max_n=20)
+    c128 = [j.P1_err_vs_c128 for j in done if not math.isnan(j.P1_c128)]
+    ns = [j.n for j in jobs]
+    return {
+        "workload": (f"{len(jobs)} requests (seed 2000), Poisson {a.serve_rate:g}/s, n~U{{10..26}} + every 20th n=30, "
+                     f"path linear/nonlinear, T~U[10,500], complex64; time cap {a.serve_cap:g} s"),
+        "requests": len(jobs),
+        "offered_within_cap": len(offered),
+        "n_mix": {str(k): ns.count(k) for k in sorted(set(ns))},
+        "served": {
+            "completed": len(done),
+            "censored_in_flight": len(cens),
+            "wall_s": res["wall_s"],
+            "solves_per_s": len(done) / res["wall_s"] if res["wall_s"] > 0 else None,
+            "p50_latency_s": p50, "p50_censored": c50,
+            "p99_latency_s": p99, "p99_censored": c99,
+            "completed_p50_latency_s": res["p50_latency_s"],
+            "completed_p99_latency_s": res["p99_latency_s"],
+            "hbm_budget_bytes": res["hbm_budget_bytes"],
+            "hbm_peak_bytes": res["hbm_peak_bytes"],
+            "by_route": res["by_route"],
+        },
+        "one_at_a_time": {
+            "completed": len(s_done),
+            "censored_in_flight": len(s_cens),
+            "wall_s": s_wall,
+            "solves_per_s": len(s_done) / s_wall if s_wall > 0 else None,
+            "p50_latency_s": sp50, "p50_censored": sc50,
+            "p99_latency_s": sp99, "p99_censored": sc99,
+        },
+        "quantiles": "nearest rank over requests that arrived within the cap; unfinished ones count as infinite "
+                     "(value null and *_censored true when the quantile falls on one)",
+        "c128_checked": len(c128),
+        "max_P1_err_vs_c128_gpu_path": max(c128) if c128 else None,
+        "_jobs": done,
     }
 
 
 def measure_xy(a, n=24, seed=3, pec=48):
-    """PEC step of the XY algorithm with the alpha = 8 catalyst (Eq. Hixy, Eq. nlpath) from the
-    Dicke state: Y products run through the general-product loop, pairs across layouts through
-    the remote gather, so it moves more than the X-driver step."""
+    """PEC step of the XY algorithm with the alpha = 8 catalyst (Eq. Hixy, Eq. nlpath), started
+    from the ground state of H^xy in the solution's Hamming-weight sector (Lanczos, complex64):
+    Y products run through the general-product loop, pairs across layouts through the remote
+    gather, so it moves more than the X-driver step."""
     import torch
 
     from instances import generate_ec3
@@ -258,7 +469,9 @@ def measure_xy(a, n=24, seed=3, pec=48):
     sched, k = HB.load_xy(ctx, inst, driver="xy", catalyst_alpha=8.0)
     ctx.set_schedule(20.0, sched)
     ctx.set_integrator(0, 0.0)
-    ctx.set_initial_state(("dicke", k))
+    t0 = time.perf_counter()
+    E0, resid, iters = HB.set_xy_ground_start(ctx, k)
+    t_ground = time.perf_counter() - t0
     ctx.propagate(4, stats=False)
     ms = []
     for _ in range(3):
@@ -268,33 +481,69 @@ def measure_xy(a, n=24, seed=3, pec=48):
     ctx.close()
     step_ms = min(ms)
     gbs = 7 * (1 << n) * 8 / (step_ms * 1e-3) / 1e9
-    return {"workload": f"XY algorithm + catalyst, EC3 n={n} seed {seed}, T=20, Dicke start, complex64",
+    return {"workload": f"XY algorithm + catalyst, EC3 n={n} seed {seed}, T=20, start: ground state of H^xy in the "
+                        f"weight-{k} sector, complex64",
+            "ground_state": {"energy": E0, "residual": resid, "lanczos_steps": iters, "seconds": t_ground},
             "pec_step_ms": step_ms, "achieved": gbs, "unit": "GB/s (7 N b per PEC step)",
             "frac": gbs / peaks()[0]}
 
 
-def measure_serving(a):
-    """Continuous batching of a seeded Poisson stream (rate 8/s): n ~ U{10..20} with every
-    20th job n = 30 (64 GiB workspace), linear/nonlinear uniform, T ~ U[2, 20] (n = 30:
-    T ~ U[0.1, 0.3]), complex64, admission by HBM budget (free memory - 2 GiB)."""
-    from paper_1311_3938_gb300 import workloads as W
+def measure_small(a, reps=30):
+    """The small-state workload alone: EC3 n = 10 seed 1, linear path, T = 20, uniform start,
+    complex128; host wall time per whole solve (initial state, every grid step, P_1 readback),
+    step by step and with CUDA-graph replays of 16 PEC steps."""
+    import statistics as S
 
-    jobs = W.random_jobs(a.serve_count, 2000, n_range=(10, 20), T_range=(2.0, 20.0), rate=8.0, big_every=20,
-                         big_n=30, path_mix=True, big_T_range=(0.1, 0.3))
-    srv = W.Server(batch_max_n=20, max_members=128, steps_per_round=16, big_chunk=32)
-    try:
-        res = srv.serve(jobs)
-    finally:
-        srv.close()
-    done = res.pop("jobs")
-    # per-result fidelity error against the FP64 (complex128) path for the n <= 14 subset
-    W.attach_fp64_errors(done, max_n=14)
-    errs = [j.P1_err_fp64 for j in done if not math.isnan(j.P1_fp64)]
-    res["fp64_checked"] = len(errs)
-    res["max_P1_err_vs_fp64"] = max(errs) if errs else None
-    res["workload"] = (f"{len(jobs)} requests, Poisson rate 8/s, n~U{{10..20}} + every 20th n=30, "
-                       "path linear/nonlinear, T~U[2,20] (n=30: U[0.1,0.3]), complex64")
-    return res
+    from instances import generate_ec3
+    from paper_1311_3938_gb300 import hamiltonians as HB
+    from paper_1311_3938_gb300.engine import Context
+    import paper_1311_3938_gb300 as P
+
+    inst = generate_ec3(10, 1)
+    out = {"workload": "ec3-n10-seed1-linear-T20-uniform, complex128, one context"}
+    for label, k in (("step_by_step", 0), ("graph_replay", 16)):
+        ctx = Context(10, P.AQC_C128)
+        ctx.set_graph_steps(k)
+        HB.load_ec3(ctx, inst)
+        ctx.set_schedule(20.0, HB.linear_schedule())
+        ctx.set_integrator(0, 0.0)
+        walls = []
+        for r in range(reps + 3):
+            l0 = ctx.launch_count()
+            t0 = time.perf_counter()
+            ctx.set_initial_state("uniform")
+            st = ctx.propagate(-1, stats=False)
+            P1 = ctx.fidelity(inst.solution)
+            dt = time.perf_counter() - t0
+            if r >= 3:
+                walls.append(dt)
+        steps = ctx.grid()[0]
+        out[label] = {"wall_ms_p50": 1e3 * S.median(walls), "wall_ms_min": 1e3 * min(walls),
+                      "grid_steps_per_s": steps / S.median(walls), "kernels_per_solve": ctx.launch_count() - l0,
+                      "graph_replays": ctx.graph_replays(), "P1": P1}
+        out["grid_steps"] = steps
+        if k:
+            out["_state"] = ctx.state()
+        ctx.close()
+    out["speedup"] = out["step_by_step"]["wall_ms_p50"] / out["graph_replay"]["wall_ms_p50"]
+    return out
+
+
+def measure_fp64_peak(device):
+    """The FP64 FMA rate measured by aqc_measure_fp64_fma (clocks sampled during it)."""
+    import torch
+
+    from paper_1311_3938_gb300 import _native as N
+
+    s = torch.cuda.current_stream(device)
+    tf, ms = N.aqc_measure_fp64_fma(device, s.cuda_stream, 1 << 12)
+    iters = int(min(1 << 24, max(1 << 12, (1 << 12) * 300.0 / max(ms, 1e-3))))  # ~0.3 s
+    clk = Clocks(device)
+    clk.start()
+    tf, ms = N.aqc_measure_fp64_fma(device, s.cuda_stream, iters)
+    clocks = clk.stop()
+    return {"tflops": tf, "ms": ms, "iters": iters, "kernel": "k_fma64: 4 CTAs x 256 threads per SM, 8 FMA chains",
+            "clocks": clocks}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -449,9 +698,50 @@ def run_ours(a):
 
     r64 = measure(P.AQC_C64)
     r128 = None if a.no_c128 else measure(P.AQC_C128)
-    batched = None if (a.no_batch or world > 1) else measure_batched(a)
-    serving = None if (a.no_serve or world > 1) else measure_serving(a)
-    xy = None if (a.no_xy or world > 1) else measure_xy(a)
+    solo = world == 1
+    fp64 = measure_fp64_peak(local) if (r128 is not None and solo) else None
+    small = None if (a.no_small or not solo) else measure_small(a)
+    # FP64 oracle solves of the checked results on the host cores, beside the GPU legs below
+    checks = None
+    if solo and not a.no_oracle_check and not (a.no_batch and a.no_serve and small is None):
+        checks = OracleChecks(max(1, (os.cpu_count() or 2) - 2))
+        if small is not None:
+            checks.submit(("small", 0), {"n": 10, "seed": 1, "nonlinear": False, "T": 20.0, "s_kind": 0})
+        if not a.no_batch:
+            for j in batched_jobs(a.batch_count):
+                if j.n <= ORACLE_MAX_N:
+                    checks.submit(("batch", j.jid), OracleChecks.spec_of(j))
+        if not a.no_serve:
+            for j in served_jobs(a.serve_count, a.serve_rate):
+                if j.n <= ORACLE_MAX_N:
+                    checks.submit(("serve", j.jid), OracleChecks.spec_of(j))
+    xy = None if (a.no_xy or not solo) else measure_xy(a)
+    batched = None if (a.no_batch or not solo) else measure_batched(a, checks)
+    serving = None if (a.no_serve or not solo) else measure_serving(a)
+    if checks is not None:
+        t0 = time.perf_counter()
+        got = checks.results(timeout=300.0)
+        wait_s = time.perf_counter() - t0
+        if batched is not None:
+            batched["oracle_check"] = oracle_errors(batched["_jobs"], "batch", got)
+        if serving is not None:
+            serving["oracle_check"] = oracle_errors(serving["_jobs"], "serve", got)
+        if small is not None and ("small", 0) in got:
+            import numpy as np
+
+            _, N_or, P1_or, psi_or = got[("small", 0)]
+            small["oracle_check"] = {
+                "state_err": float(np.linalg.norm(small["_state"] - psi_or) / np.linalg.norm(psi_or)),
+                "P1_err": abs(small["graph_replay"]["P1"] - P1_or), "grid_steps_equal": N_or == small["grid_steps"],
+                "state_bar": 1e-10}
+        oracle_note = {"workers": checks.workers, "submitted": len(checks.pending), "finished": len(got),
+                       "extra_wait_s": wait_s}
+    else:
+        oracle_note = None
+    for leg in (batched, serving, small):
+        if leg is not None:
+            leg.pop("_jobs", None)
+            leg.pop("_state", None)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         gbs, cores, desc, _ = cpu_sample()
@@ -512,12 +802,18 @@ def run_ours(a):
         "gpu_launches": r64["launches"],
         "clocks": r64["clocks"],
         "fidelity_P1_window": r64["P1"],
+        "small_state": small,
         "batched": batched,
         "serving": serving,
+        "oracle_checks": oracle_note,
         "xy_algorithm": xy,
     }
     if r128 is not None:
         flops = pec_flops_c128(n) * (1 << n)
+        if fp64 is not None:
+            fp64_peak, fp64_kind = fp64["tflops"], "measured in this run (aqc_measure_fp64_fma)"
+        else:
+            fp64_peak, fp64_kind = 1.25, "nominal FP64 (no measurement in this run)"
         line["c128"] = {
             "dtype": "f64",
             "value": r128["value"],
@@ -527,12 +823,13 @@ def run_ours(a):
             "roofline": {
                 "bound": "alu",
                 "achieved": flops / (r128["pec_step_ms"] * 1e-3) / 1e12,
-                "peak": 1.25,
-                "peak_kind": "nominal FP64 (profiling recipe)",
+                "peak": fp64_peak,
+                "peak_kind": fp64_kind,
                 "unit": "TFLOP/s",
-                "frac": flops / (r128["pec_step_ms"] * 1e-3) / 1e12 / 1.25,
+                "frac": flops / (r128["pec_step_ms"] * 1e-3) / 1e12 / fp64_peak,
                 "hbm_frac": r128["pec_step_gbs"] / hbm_peak,
                 "traffic": profiled_traffic("c128", n),
+                "fp64_fma_measurement": fp64,
             },
             "e2e": r128.get("e2e"),
             "gpu_launches": r128["launches"],

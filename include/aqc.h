@@ -223,6 +223,22 @@ int aqc_set_relabel(aqc_ctx *ctx, int enable);
  * integrator. */
 int aqc_set_slab_bits(aqc_ctx *ctx, int slab_bits);
 
+/* CUDA-graph replay of the PEC steps of Sec. I.B on the fixed-step grid: K consecutive steps
+ * (all their layout passes) are captured once into a graph on a library-owned stream and
+ * replayed on the context stream, K steps per host call, which removes the per-launch host
+ * cost that dominates small states.  Before each replay one small kernel writes the K steps'
+ * schedule weights, computed on the host by the same expression as the step-by-step path, into
+ * the workspace; results are bit-identical to k_steps = 0.  k_steps: 0 = off, -1 = automatic
+ * (default: K = 16 for n <= 20, off above), or a multiple of 4 in [4, 64].  The graph is
+ * recaptured when the tables, the step size or the vectors change, and is not used under
+ * step-size control, the slab order or a clause-by-clause sequence (those steps run one by
+ * one).  Grid steps that remain after the last whole replay run one by one.  AQC_E_INVAL for
+ * other k_steps; a failed capture returns AQC_E_CUDA from aqc_propagate. */
+int aqc_set_graph_steps(aqc_ctx *ctx, int k_steps);
+
+/* Graph replays (aqc_set_graph_steps) the context has issued since creation. */
+int aqc_get_graph_replays(const aqc_ctx *ctx, int64_t *out);
+
 /* Set psi(0) and reset the integrator to t = 0.  kind = AQC_INIT_*; `basis` is the index for
  * AQC_INIT_BASIS and the Hamming weight k (0..n) for AQC_INIT_DICKE (the balanced superposition
  * of all basis states with k one-bits, the ground state of Eq. Hixyz in that sector);
@@ -399,11 +415,21 @@ int aqc_tridiag_eigvals(int k, const double *a, const double *b, int n_eig, doub
  * pointers are rejected with AQC_E_INVAL; errors are described by aqc_last_error(NULL). */
 int aqc_norm2_noalloc(int precision, const void *psi, uint64_t n_amplitudes, void *cuda_stream, double *out);
 
+/* ---- measurement ---------------------------------------------------------------------- */
+
+/* The FP64 FMA rate of `device` in TFLOP/s (2 flops per FMA), the denominator of the
+ * complex128 PEC step's ALU roofline: one warm-up launch, then one timed launch (CUDA events on
+ * `cuda_stream`) of 4 CTAs of 256 threads per SM, each thread running 8 independent FMA chains
+ * for `iters` rounds.  Synchronises the stream; *ms_out (nullable) receives the timed launch's
+ * duration.  iters in [1, 2^24], else AQC_E_INVAL; errors are described by
+ * aqc_last_error(NULL).  The paper has no counterpart. */
+int aqc_measure_fp64_fma(int device, void *cuda_stream, int iters, double *tflops_out, double *ms_out);
+
 /* Total kernel launches the context has issued since creation (monotone counter). */
 int aqc_launch_count(const aqc_ctx *ctx, int64_t *out);
 
-/* Message of the last error of ctx (or, for ctx == NULL, of the last failed aqc_create or
- * aqc_norm2_noalloc on the calling thread). */
+/* Message of the last error of ctx (or, for ctx == NULL, of the last failed aqc_create,
+ * aqc_norm2_noalloc or aqc_measure_fp64_fma on the calling thread). */
 const char *aqc_last_error(const aqc_ctx *ctx);
 
 /* Library version string. */

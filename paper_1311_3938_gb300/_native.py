@@ -112,6 +112,9 @@ def lib():
             "aqc_tridiag_eigvals": (i32, [i32, C.POINTER(dbl), C.POINTER(dbl), i32, C.POINTER(dbl)]),
             "aqc_tridiag_eigvec": (i32, [i32, C.POINTER(dbl), C.POINTER(dbl), dbl, C.POINTER(dbl)]),
             "aqc_launch_count": (i32, [vp, C.POINTER(i64)]),
+            "aqc_set_graph_steps": (i32, [vp, i32]),
+            "aqc_measure_fp64_fma": (i32, [i32, vp, i32, C.POINTER(dbl), C.POINTER(dbl)]),
+            "aqc_get_graph_replays": (i32, [vp, C.POINTER(i64)]),
             "aqc_batch_workspace_bytes": (sz, [i32, i64]),
             "aqc_batch_create": (i32, [C.POINTER(vp), i32, i32, i32, i64, vp, sz, vp]),
             "aqc_batch_destroy": (None, [vp]),
@@ -322,6 +325,24 @@ def aqc_tridiag_eigvec(a, b, lam):
     if rc:
         raise AqcError(rc, "aqc_tridiag_eigvec: bad arguments")
     return list(out)
+
+
+def aqc_set_graph_steps(ctx, k_steps):
+    _check(ctx, lib().aqc_set_graph_steps(ctx, int(k_steps)))
+
+
+def aqc_get_graph_replays(ctx):
+    out = C.c_int64()
+    _check(ctx, lib().aqc_get_graph_replays(ctx, C.byref(out)))
+    return out.value
+
+
+def aqc_measure_fp64_fma(device, stream_ptr, iters):
+    """(TFLOP/s, ms of the timed launch)."""
+    tf = C.c_double()
+    ms = C.c_double()
+    _check(None, lib().aqc_measure_fp64_fma(int(device), C.c_void_p(stream_ptr), int(iters), C.byref(tf), C.byref(ms)))
+    return tf.value, ms.value
 
 
 def aqc_launch_count(ctx):

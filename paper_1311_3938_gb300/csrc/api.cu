@@ -87,7 +87,7 @@ std::vector<Layout> layouts_for(int n, int prec, int tile_bits, bool allow_clust
 
 
 struct WsPlan {
-  size_t off_tab, off_slots, off_counter, off_sync, off_perm, off_partials, off_dcode, off_vec, vec_bytes, total;
+  size_t off_tab, off_slots, off_counter, off_sync, off_perm, off_wdev, off_partials, off_dcode, off_vec, vec_bytes, total;
   size_t partial_doubles;
 };
 
@@ -99,7 +99,8 @@ WsPlan plan_workspace(int n, int prec, unsigned flags = 0) {
   w.off_counter = w.off_slots + 256;
   w.off_sync = w.off_counter + 256;  // slab work counter + per-slab counters
   w.off_perm = w.off_sync + align_up((1 + kMaxSlabs) * sizeof(unsigned), 256);  // bit-permutation tables
-  w.off_partials = w.off_perm + 4 * 256 * sizeof(uint32_t);
+  w.off_wdev = w.off_perm + 4 * 256 * sizeof(uint32_t);  // weights of graph-replayed steps
+  w.off_partials = w.off_wdev + align_up(3 * kMaxGraphSteps * sizeof(double), 256);
   // k_apply grids are persistent (at most kMaxApplyGrid CTAs); k_norm2 uses reduce_grid()
   size_t g = std::max((size_t)kMaxApplyGrid, (size_t)reduce_grid((uint64_t)1 << n));
   w.partial_doubles = 3 * g;
@@ -190,6 +191,25 @@ struct aqc_ctx {
   int64_t seg_done0 = 0;    // accepted steps before the current segment
   std::vector<aqc_segment> segs;
   int64_t launches = 0;  // kernel launches issued (monotone counter)
+
+  // CUDA-graph replay of K PEC steps (fixed-step grid, no slab order, no clause-by-clause
+  // sequence): captured once on a private stream, replayed on `stream` after the host has
+  // written the K steps' weights to d_wdev
+  int graph_req = -1;             // 0 off, -1 automatic, K > 0 (a multiple of 4, <= kMaxGraphSteps)
+  double* d_wdev = nullptr;       // 3 K weights of the replayed steps
+  const double* cur_wdev = nullptr;  // set while a capture is issuing step j: d_wdev + 3 j
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  struct GraphKey {
+    int K = 0, phase = 0;
+    double h = 0.0;
+    int64_t tables = -1;
+    uint32_t n_slabs = 0;
+    void* vec[V_COUNT] = {};
+  } gkey;
+  int64_t g_launches = 0;         // kernel launches in one replay
+  int64_t graph_replays = 0;
+  int64_t tables_version = 0;     // bumped by every table build
 
   std::string err;
 };
@@ -397,6 +417,7 @@ void plan_slabs(aqc_ctx* c) {
 }
 
 int build_tables(aqc_ctx* c) {
+  c->tables_version++;
   plan_layouts(c);
   DevTables* t = c->h_tab;
   memset(t, 0, sizeof(DevTables));
@@ -716,6 +737,7 @@ int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, vo
     p.with_remote = first;
     for (int g = 0; g < 3; g++) p.w[g] = w[g];
     p.src = src;
+    p.wdev = c->cur_wdev;
     p.qin = first ? nullptr : c->vec[V_Q];
     if (!last) {
       p.mode = MODE_PARTIAL;
@@ -735,6 +757,7 @@ int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, vo
         x.L = p.L;
         x.layout_index = l;
         for (int g = 0; g < 3; g++) x.w[g] = w[g];
+        x.wdev = c->cur_wdev;
         x.qin = p.qin;
         x.qout = p.qout;
         x.ntiles = p.ntiles;
@@ -939,6 +962,106 @@ int control_step(aqc_ctx* c) {
     c->segs.back().end = AQC_SEG_GREW;
     return begin_segment(c, c->seg_t0 + (double)c->step * c->h, 2.0 * c->h);
   }
+  return AQC_OK;
+}
+
+// ---- CUDA-graph replay of PEC steps ---------------------------------------------------------
+// A replay covers K consecutive PEC steps starting at a step index of the captured phase
+// (index mod 4 selects the derivative ring slots).  Everything a captured launch bakes in -- the
+// vectors, h, the tables' layouts and shapes -- is in the key; the weights are not: the host
+// computes them (sched_weights, the expression the eager steps use, so both give the same
+// bits) and writes them to d_wdev ahead of each replay.
+
+int graph_k(const aqc_ctx* c) {
+  if (c->adaptive || c->in_batch || c->slab.n_slabs || c->step_class >= 0) return 0;
+  if (c->graph_req < 0) return c->n <= 20 ? 16 : 0;  // launch-bound sizes
+  return c->graph_req;
+}
+
+aqc_ctx::GraphKey graph_key(const aqc_ctx* c, int K) {
+  aqc_ctx::GraphKey k;
+  k.K = K;
+  k.phase = (int)(c->step & 3);
+  k.h = c->h;
+  k.tables = c->tables_version;
+  k.n_slabs = c->slab.n_slabs;
+  for (int v = 0; v < V_COUNT; v++) k.vec[v] = c->vec[v];
+  return k;
+}
+
+bool same_key(const aqc_ctx::GraphKey& a, const aqc_ctx::GraphKey& b) {
+  if (a.K != b.K || a.phase != b.phase || memcmp(&a.h, &b.h, sizeof(double)) != 0 || a.tables != b.tables ||
+      a.n_slabs != b.n_slabs)
+    return false;
+  for (int v = 0; v < V_COUNT; v++)
+    if (a.vec[v] != b.vec[v]) return false;
+  return true;
+}
+
+void drop_step_graph(aqc_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->gkey = aqc_ctx::GraphKey();
+}
+
+// Capture K PEC steps from the current step on the private stream; host counters are left as
+// they were (the replay advances them).
+int capture_steps(aqc_ctx* c, int K) {
+  drop_step_graph(c);
+  if (!c->cap_stream) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  const int64_t step0 = c->step, evals0 = c->evals, launches0 = c->launches;
+  cudaStream_t user = c->stream;
+  c->stream = c->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  int rc = AQC_OK;
+  if (e == cudaSuccess) {
+    for (int j = 0; j < K && rc == AQC_OK; j++) {
+      c->cur_wdev = c->d_wdev + 3 * j;
+      rc = pec_step(c);
+      c->step++;
+    }
+    c->cur_wdev = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e_end = e == cudaSuccess ? cudaStreamEndCapture(c->cap_stream, &graph) : e;
+  c->stream = user;
+  c->g_launches = c->launches - launches0;
+  c->step = step0;
+  c->evals = evals0;
+  c->launches = launches0;
+  if (rc != AQC_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess || e_end != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    FAIL(c, AQC_E_CUDA, "capture of %d PEC steps: %s", K, cudaGetErrorString(e != cudaSuccess ? e : e_end));
+  }
+  e = cudaGraphInstantiate(&c->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    c->gexec = nullptr;
+    FAIL(c, AQC_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  c->gkey = graph_key(c, K);
+  return AQC_OK;
+}
+
+// K PEC steps of the fixed-step grid as one graph replay (the caller checked that K steps
+// remain in the segment and in the call's step budget).
+int pec_steps_graph(aqc_ctx* c, int K) {
+  if (!c->gexec || !same_key(graph_key(c, K), c->gkey)) {
+    int rc = capture_steps(c, K);
+    if (rc) return rc;
+  }
+  double wb[3 * kMaxGraphSteps];
+  for (int j = 0; j < K; j++) sched_weights(c, c->seg_t0 + (double)(c->step + j + 1) * c->h, wb + 3 * j);
+  CUDA_TRY(c, launch_set_weights(c->d_wdev, wb, 3 * K, c->stream));
+  CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->stream));
+  c->launches += 1 + c->g_launches;
+  c->evals += K;
+  c->graph_replays++;
+  for (int j = 0; j < K; j++) count_step(c);
   return AQC_OK;
 }
 
@@ -1190,6 +1313,7 @@ int aqc_create(aqc_ctx** out, int device, int precision, int n_qubits, void* wor
   c->d_sync = (unsigned*)(c->ws + wp.off_sync);
   c->d_perm = (uint32_t*)(c->ws + wp.off_perm);
   c->d_partials = (double*)(c->ws + wp.off_partials);
+  c->d_wdev = (double*)(c->ws + wp.off_wdev);
   c->d_dcode = (uint8_t*)(c->ws + wp.off_dcode);
   for (int v = 0; v < V_COUNT; v++) c->vec[v] = c->ws + wp.off_vec + (size_t)v * wp.vec_bytes;
   if (workspace_bytes >= plan_workspace(n_qubits, precision, AQC_WS_STEP_CONTROL).total)
@@ -1213,6 +1337,8 @@ void aqc_destroy(aqc_ctx* ctx) {
   {
     DeviceGuard dg(ctx->device);
     release_transfers(ctx);
+    drop_step_graph(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   }
   delete ctx->h_tab;
   delete ctx;
@@ -1308,6 +1434,61 @@ int aqc_set_relabel(aqc_ctx* ctx, int enable) {
   if (!ctx) return AQC_E_INVAL;
   ctx->relabel = enable ? 1 : 0;
   ctx->dirty = true;  // a state already set moves to the new order at the next table build
+  return AQC_OK;
+}
+
+int aqc_set_graph_steps(aqc_ctx* ctx, int k_steps) {
+  if (!ctx) return AQC_E_INVAL;
+  if (!(k_steps == -1 || k_steps == 0 || (k_steps >= 4 && k_steps <= kMaxGraphSteps && k_steps % 4 == 0)))
+    FAIL(ctx, AQC_E_INVAL, "k_steps must be -1, 0 or a multiple of 4 in [4, %d]", kMaxGraphSteps);
+  ctx->graph_req = k_steps;
+  DeviceGuard dg(ctx->device);
+  drop_step_graph(ctx);
+  return AQC_OK;
+}
+
+int aqc_measure_fp64_fma(int device, void* cuda_stream, int iters, double* tflops_out, double* ms_out) {
+  if (!tflops_out || iters < 1 || iters > (1 << 24)) {
+    g_create_error = "tflops_out must be non-NULL and iters in [1, 2^24]";
+    return AQC_E_INVAL;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    g_create_error = "no such CUDA device";
+    return AQC_E_CUDA;
+  }
+  DeviceGuard dg(device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    g_create_error = "cudaDeviceGetAttribute failed";
+    return AQC_E_CUDA;
+  }
+  const int blocks = 4 * sms;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = launch_fma64(blocks, iters / 8 + 1, s);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) e = launch_fma64(blocks, iters, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess || !(ms > 0.f)) {
+    g_create_error = std::string("FP64 FMA timing: ") + cudaGetErrorString(e);
+    return AQC_E_CUDA;
+  }
+  *tflops_out = 2.0 * (double)fma64_count(blocks, iters) / ((double)ms * 1e-3) / 1e12;
+  if (ms_out) *ms_out = ms;
+  return AQC_OK;
+}
+
+int aqc_get_graph_replays(const aqc_ctx* ctx, int64_t* out) {
+  if (!ctx || !out) return AQC_E_INVAL;
+  *out = ctx->graph_replays;
   return AQC_OK;
 }
 
@@ -1455,6 +1636,12 @@ int aqc_propagate(aqc_ctx* ctx, int64_t max_steps, aqc_stats* stats) {
       if (!ctx->hist_ready) {
         rc = start_history(ctx);
         if (rc) break;
+      }
+      const int K = graph_k(ctx);
+      if (K > 0 && ctx->seg_m - ctx->step >= K && target - ctx->steps_done >= K) {
+        rc = pec_steps_graph(ctx, K);
+        if (rc) break;
+        continue;
       }
       rc = pec_step(ctx);
       if (!rc) {

@@ -110,6 +110,8 @@ struct ApplyParams {
   int mode;
   int stage;         // RK4 stage 1..4
   double w[3];       // group weights A, B, C at the evaluation time
+  const double* wdev; // nullable: read the weights from this device array instead of w (steps
+                      // replayed from a CUDA graph, whose weights the host writes before a replay)
   double h;
   const uint8_t* dcode; // per-index clause counts of class table_class (nullable)
   const void* src;   // vector the Hamiltonian acts on
@@ -166,6 +168,7 @@ struct XPartialParams {
   Layout L;
   int layout_index;
   double w[3];
+  const double* wdev;    // nullable: weights from device memory (as ApplyParams::wdev)
   const void* qin;       // nullable
   void* qout;
   uint32_t ntiles;
@@ -228,6 +231,10 @@ constexpr int kSlotDotIm = 4;
 constexpr int kSlotFault = 5;  // nonzero: an inter-CTA wait gave up (results of that step are invalid)
 constexpr int kSlotCount = 8;
 
+// PEC steps per CUDA-graph replay of a lone context: at most this many; the weights of each
+// replayed step come from a device array of 3 doubles per step (ApplyParams::wdev)
+constexpr int kMaxGraphSteps = 64;
+
 cudaError_t launch_apply(int prec, const ApplyParams& p, int smem_bytes, cudaStream_t s);
 int apply_grid(int prec, int mode, uint32_t ntiles, int smem_bytes);
 size_t apply_smem_bytes(int prec, int t, int n_plain, int n_general, int n_z);
@@ -250,6 +257,13 @@ cudaError_t launch_predict(int prec, void* p, const void* y, const void* f3, con
 cudaError_t launch_reduce(int prec, int what, const void* a, uint64_t N, double* partials, unsigned* counter,
                           double* slots, int grid, cudaStream_t s);
 cudaError_t launch_fidelity(int prec, const void* a, uint64_t w, double* slots, cudaStream_t s);
+// dst[0 .. count) = w[0 .. count), count <= 3 kMaxGraphSteps, the values passed as kernel
+// arguments (no host buffer outlives the call)
+cudaError_t launch_set_weights(double* dst, const double* w, int count, cudaStream_t s);
+// k_fma64: `blocks` CTAs of 256 threads, each thread `iters` rounds of independent FP64 FMAs;
+// fma64_count gives the FMAs one launch performs
+cudaError_t launch_fma64(int blocks, int iters, cudaStream_t s);
+int64_t fma64_count(int blocks, int iters);
 int reduce_grid(uint64_t N);
 cudaError_t launch_batch(int prec, int threads, const BatchLaunch& b, int nitems, int smem, cudaStream_t s);
 

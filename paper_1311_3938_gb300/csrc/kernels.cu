@@ -871,8 +871,8 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_PARTIAL && sizeof(R) =
   using C2 = typename Cplx<R>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   TileCtx<R> T;
-  load_coefficients<R>(T, P.tab, P.L, P.layout_index, P.with_diag != 0, P.with_remote != 0, P.dcode, P.w[0], P.w[1],
-                       P.w[2], smem);
+  const double w0 = P.wdev ? P.wdev[0] : P.w[0], w1 = P.wdev ? P.wdev[1] : P.w[1], w2 = P.wdev ? P.wdev[2] : P.w[2];
+  load_coefficients<R>(T, P.tab, P.L, P.layout_index, P.with_diag != 0, P.with_remote != 0, P.dcode, w0, w1, w2, smem);
   T.stage = P.stage;
   T.h = (R)P.h;
   set_h24(T, P.h);
@@ -1390,6 +1390,51 @@ cudaError_t launch_predict(int prec, void* p, const void* y, const void* f3, con
   else
     k_predict<float><<<grid, 256, 0, s>>>((float2*)p, (const float2*)y, (const float2*)f3, (const float2*)f2,
                                           (const float2*)f1, (const float2*)f0, (float)h, N);
+  return cudaGetLastError();
+}
+
+// ---- FP64 FMA throughput (the denominator of the complex128 step's ALU roofline) -------
+__device__ double g_fma_sink;
+
+// kFmaChains independent FMA chains per thread (enough to cover the FP64 pipe's latency); the
+// result is stored only if it takes a value it never takes, so the chains stay live
+constexpr int kFmaChains = 8;
+__global__ void __launch_bounds__(256) k_fma64(int iters, double m, double c) {
+  double a[kFmaChains];
+#pragma unroll
+  for (int k = 0; k < kFmaChains; k++) a[k] = 1.0 + 1e-3 * k + 1e-9 * threadIdx.x;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int k = 0; k < kFmaChains; k++) a[k] = fma(a[k], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kFmaChains; k++) s += a[k];
+  if (s == -1.0) g_fma_sink = s;
+}
+
+cudaError_t launch_fma64(int blocks, int iters, cudaStream_t s) {
+  k_fma64<<<blocks, 256, 0, s>>>(iters, 0.999999999, 1e-12);
+  return cudaGetLastError();
+}
+
+int64_t fma64_count(int blocks, int iters) { return (int64_t)blocks * 256 * kFmaChains * iters; }
+
+struct GraphWeights {
+  double w[3 * kMaxGraphSteps];
+};
+
+__global__ void k_set_weights(double* dst, const GraphWeights W, int count) {
+  const int i = (int)threadIdx.x;
+  if (i < count) dst[i] = W.w[i];
+}
+
+cudaError_t launch_set_weights(double* dst, const double* w, int count, cudaStream_t s) {
+  if (count < 0 || count > 3 * kMaxGraphSteps) return cudaErrorInvalidValue;
+  GraphWeights W;
+  for (int i = 0; i < count; i++) W.w[i] = w[i];
+  for (int i = count; i < 3 * kMaxGraphSteps; i++) W.w[i] = 0.0;
+  k_set_weights<<<1, 3 * kMaxGraphSteps, 0, s>>>(dst, W, count);
   return cudaGetLastError();
 }
 

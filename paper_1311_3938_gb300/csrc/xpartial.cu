@@ -137,6 +137,7 @@ __device__ __forceinline__ void reg_hop(float c, const float4 (&own)[8], const u
 }
 
 __device__ __forceinline__ double weight_of(const XPartialParams& P, int g) {
+  if (P.wdev) return P.wdev[g];
   return g == 0 ? P.w[0] : (g == 1 ? P.w[1] : P.w[2]);
 }
 

@@ -105,6 +105,13 @@ class Context:
         """Slab order of the PEC step: 0 off, -1 automatic, k > 0 at most k slab bits."""
         N.aqc_set_slab_bits(self.handle, slab_bits)
 
+    def set_graph_steps(self, k_steps=-1):
+        """PEC steps per CUDA-graph replay: 0 off, -1 automatic, or a multiple of 4 up to 64."""
+        N.aqc_set_graph_steps(self.handle, k_steps)
+
+    def graph_replays(self):
+        return N.aqc_get_graph_replays(self.handle)
+
     def set_integrator(self, n_steps=0, kappa=0.0, adaptive=False, tol=0.0):
         """Fixed-step grid (n_steps, or the step rule with kappa), or step-size control with a
         relative tolerance tol per PEC step (adaptive=True; aqc.h, aqc_set_integrator)."""

@@ -134,8 +134,8 @@ def load_xy(ctx, inst, driver: str = "xy", catalyst_alpha: float = 0.0, removed:
     group A, H_f clauses in group B and, if catalyst_alpha != 0, H_{m-1} (every clause but
     `removed`; default: the last removable clause) in group C; or, with clause_by_clause, the
     clauses in stored order as the sequence of Eq. kpath in group C (Eq. cbc).  Returns the
-    schedule (use with ctx.set_schedule) and the Hamming weight of the solution (the Dicke
-    start sector)."""
+    schedule (use with ctx.set_schedule) and the Hamming weight of the solution (the start
+    sector: set_xy_ground_start for the XY driver, the Dicke state for XYZ)."""
     terms = xy_driver_terms(inst.clauses) if driver == "xy" else xyz_driver_terms(inst.clauses)
     ctx.load_terms(N.AQC_GRP_A, *terms)
     ctx.load_clauses(N.AQC_GRP_B, inst.clauses, penalty=penalty)
@@ -152,6 +152,30 @@ def load_xy(ctx, inst, driver: str = "xy", catalyst_alpha: float = 0.0, removed:
         ctx.load_clauses(N.AQC_GRP_C, keep, penalty=penalty)
         sched = nonlinear_schedule(catalyst_alpha)
     return sched, bin(int(inst.solution)).count("1")
+
+
+def set_xy_ground_start(ctx, k: int, max_iter: int = 200, tol: float = None):
+    """psi(0) of the XY algorithm (Sec. III.A.3): the ground state of H(0) in the sector of
+    Hamming weight k.  On the XY paths here H(0) is the driver H^xy alone (weight 1 for group A,
+    0 for B and for the catalyst; the clause-by-clause term H_d(0) vanishes).  The eigenpair is
+    computed by aqc_lanczos_ground from the Dicke state of weight k (Eq. initstate), which lies
+    in the sector and overlaps the ground state: the sector block of H^xy has non-positive
+    off-diagonal entries, so its ground state has positive amplitudes.  tol is the relative Ritz
+    residual (default 1e-12 for complex128, 2e-6 for complex64); the Krylov space is capped at
+    the sector dimension C(n, k).  Returns (energy, residual ||H x - E x||, iterations)."""
+    import math
+
+    if not 0 <= k <= ctx.n:
+        raise ValueError("Hamming weight out of range")
+    if tol is None:
+        tol = 1e-12 if ctx.precision == N.AQC_C128 else 2e-6
+    ctx.set_initial_state(("dicke", k))
+    start = ctx.state(device=True)
+    iters = max(1, min(int(max_iter), math.comb(ctx.n, k)))
+    x, theta, resid, used = ctx.lanczos_ground(0.0, start, max_iter=iters, tol=tol)
+    del start
+    ctx.set_initial_state(x)
+    return theta, resid, used
 
 
 def clause_bits(clauses):

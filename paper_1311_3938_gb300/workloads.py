@@ -37,7 +37,8 @@ class Job:
     precision: int = N.AQC_C64
     s_kind: int = N.AQC_S_LINEAR
     arrival: float = 0.0
-    driver: str = "x"      # "x" (Eq. Hix, start |S>), "xy" / "xyz" (Eq. Hixy / Hixyz, Dicke start)
+    driver: str = "x"      # "x" (Eq. Hix, start |S>); "xy" (Eq. Hixy, start: its sector ground
+                           # state); "xyz" (Eq. Hixyz, start: the Dicke state, its sector ground state)
     alpha: float = 8.0     # catalyst strength of the XY/XYZ nonlinear path (Eq. nlpath)
     hard: bool = False     # instance by the hard-instance recipe of Sec. I.E
     # filled in when the job is served
@@ -48,13 +49,15 @@ class Job:
     norm2: float = math.nan
     steps: int = 0
     route: str = ""
-    P1_fp64: float = math.nan  # the same job on the complex128 (FP64) path, if checked
+    keep: bool = False         # keep the final state (job.state) when the job finishes
+    P1_c128: float = math.nan  # the same job re-solved on the GPU's complex128 path, if checked
     state: np.ndarray = field(default=None, repr=False)
 
     @property
-    def P1_err_fp64(self):
-        """|P_1 - P_1(FP64)|: the fidelity error of this result against the FP64 path."""
-        return abs(self.P1 - self.P1_fp64)
+    def P1_err_vs_c128(self):
+        """|P_1 - P_1(complex128 GPU path)|: this result's fidelity against the library's own
+        FP64 path (a check of the FP32 state's rounding, not an independent reference)."""
+        return abs(self.P1 - self.P1_c128)
 
     @property
     def latency(self):
@@ -89,7 +92,10 @@ def make_context(job: Job, device=0, stream=None, tile_bits=0) -> tuple:
         sched, k = HB.load_xy(ctx, inst, driver=job.driver, catalyst_alpha=job.alpha if job.nonlinear else 0.0)
         ctx.set_schedule(job.T, sched, job.s_kind)
         ctx.set_integrator(0, 0.0)
-        ctx.set_initial_state(("dicke", k))
+        if job.driver == "xy":
+            HB.set_xy_ground_start(ctx, k)
+        else:
+            ctx.set_initial_state(("dicke", k))
     return ctx, inst
 
 
@@ -97,7 +103,7 @@ def _finish(job: Job, ctx: Context, inst, keep_state: bool):
     job.P1 = ctx.fidelity(inst.solution)
     job.E = ctx.energy(N.AQC_GRP_B)
     job.norm2 = ctx.norm2()
-    if keep_state:
+    if keep_state or job.keep:
         job.state = ctx.state()
 
 
@@ -178,19 +184,21 @@ def _nsteps(ctx, job):
     return ctx._nsteps
 
 
-def attach_fp64_errors(jobs, max_n=20, device=0):
-    """For complex64 results with n <= max_n, solve the same job on the complex128 (FP64)
-    path and store its P_1, so each result states its fidelity error against FP64."""
+def attach_c128_errors(jobs, min_n=0, max_n=20, device=0):
+    """For complex64 results with min_n <= n <= max_n, solve the same job on the library's
+    complex128 path and store its P_1 (job.P1_c128), so each result states how far its FP32
+    state's rounding moved the fidelity."""
     import copy
 
     for job in jobs:
-        if job.precision != N.AQC_C64 or job.n > max_n or math.isnan(job.P1):
+        if job.precision != N.AQC_C64 or not (min_n <= job.n <= max_n) or math.isnan(job.P1):
             continue
         ref = copy.deepcopy(job)
         ref.precision = N.AQC_C128
         ref.state = None
+        ref.keep = False
         solve_single(ref, device)
-        job.P1_fp64 = ref.P1
+        job.P1_c128 = ref.P1
     return jobs
 
 
@@ -226,6 +234,47 @@ def run_sweep_n20(seed=2, n=20, Ts=(10.0, 50.0, 200.0), device=0):
                     "seconds_c64": t64,
                 })
     return rows
+
+
+def serve_one_at_a_time(jobs, device=0, time_limit=None, chunk_amplitude_steps=1 << 26):
+    """The one-at-a-time baseline of a request stream: jobs in arrival order, each alone on the
+    GPU (one context), started when it has arrived and the previous one is done; propagated in
+    chunks of about `chunk_amplitude_steps` / 2^n grid steps so that a time limit ends the run
+    between chunks (the job then in progress is censored).  Returns (finished jobs, censored
+    jobs, wall seconds)."""
+    pending = sorted(jobs, key=lambda j: j.arrival)
+    done, censored = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    now = lambda: time.perf_counter() - t0  # noqa: E731
+    for job in pending:
+        if time_limit and now() > time_limit:
+            break
+        wait = job.arrival - now()
+        if wait > 0:
+            if time_limit and job.arrival > time_limit:
+                break
+            time.sleep(wait)
+        job.admitted = now()
+        ctx, inst = make_context(job, device)
+        chunk = max(16, chunk_amplitude_steps >> job.n)
+        total = _nsteps(ctx, job)
+        steps = 0
+        while steps < total and not (time_limit and now() > time_limit):
+            ctx.propagate(min(chunk, total - steps), stats=False)
+            ctx.stream.synchronize()
+            steps = min(total, steps + chunk)
+        if steps < total:
+            ctx.close()
+            censored.append(job)
+            break
+        job.steps = total
+        job.route = "single"
+        _finish(job, ctx, inst, False)
+        job.finished = now()
+        ctx.close()
+        done.append(job)
+    return done, censored, now()
 
 
 def run_sequential(jobs, device=0, keep_state=False):
@@ -268,9 +317,10 @@ def run_batch512(count=512, seed=1000, device=0, sample_every=16):
 
 
 def run_algorithms(n=13, seed=3, Ts=(2.0, 5.0, 10.0, 20.0, 50.0), precision=N.AQC_C64, device=0):
-    """The algorithms of Sec. III-IV on one instance: X (from |S>), XYZ and XY (from the Dicke
-    state of the solution's weight), and XY with the alpha = 8 catalyst (Eq. nlpath), each over
-    runtimes T: final P_1, energy E and wall seconds per solve."""
+    """The algorithms of Sec. III-IV on one instance: X (from |S>), XYZ (from the Dicke state of
+    the solution's weight), XY (from the ground state of H^xy in that sector) and XY with the
+    alpha = 8 catalyst (Eq. nlpath), each over runtimes T: final P_1, energy E and wall seconds
+    per solve (the start-state preparation included)."""
     rows = []
     for driver, nonlinear in (("x", False), ("xyz", False), ("xy", False), ("xy", True)):
         for T in Ts:
@@ -506,6 +556,21 @@ class Server:
             if not in_batch and big and all(len(e[6]) >= 2 or e[4] is not None for e in big):
                 time.sleep(2e-4)  # only large jobs in flight: do not spin
         wall = now()
+        # a time limit leaves work in flight: release it (those requests are censored)
+        censored = []
+        for slot in list(in_batch):
+            job, ctx, inst = in_batch.pop(slot)
+            self.batch.remove(slot)
+            ctx.close()
+            self.used -= job.workspace_bytes()
+            censored.append(job)
+        for entry in big:
+            job, ctx, inst, stream = entry[0], entry[1], entry[2], entry[3]
+            stream.synchronize()
+            ctx.close()
+            self.used -= job.workspace_bytes()
+            censored.append(job)
+        big.clear()
         lat = np.array([j.latency for j in done]) if done else np.array([math.nan])
         by_route = {}
         for route in ("batch", "stream"):
@@ -525,6 +590,8 @@ class Server:
             "by_route": by_route,
             "loop": prof,
             "jobs": done,
+            "censored_jobs": censored,   # admitted, unfinished at the time limit
+            "not_admitted": pending,     # arrived (or not yet) and never admitted
         }
 
     def close(self):

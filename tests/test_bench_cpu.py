@@ -42,3 +42,40 @@ def test_committed_traffic_profile_fields():
 def test_short_oracle_sample():
     gbs, cores, desc, secs = bench.cpu_sample(1.0)
     assert gbs > 0 and cores >= 1 and "oracle" in desc.lower()
+
+
+def test_censored_quantiles():
+    inf = float("inf")
+    assert bench.quantile_censored([3.0, 1.0, 2.0], 0.5) == (2.0, False)
+    assert bench.quantile_censored([3.0, 1.0, 2.0, inf], 0.5) == (2.0, False)
+    assert bench.quantile_censored([3.0, 1.0, 2.0, inf], 0.99) == (None, True)
+    assert bench.quantile_censored(list(range(1, 201)), 0.99) == (198, False)
+    assert bench.quantile_censored([], 0.5) == (None, False)
+
+
+def test_oracle_checks_in_spawned_workers_and_error_rows():
+    """The host-side checker: two spawned workers solve small specs; the comparison rows of
+    oracle_errors take the state of a finished job (here: the oracle's own, perturbed)."""
+    import numpy as np
+
+    from paper_1311_3938_gb300.workloads import Job
+
+    checks = bench.OracleChecks(2)
+    specs = {k: {"n": 6 + k, "seed": 1 + k, "nonlinear": bool(k % 2), "T": 2.0, "s_kind": k % 2} for k in range(3)}
+    for k, sp in specs.items():
+        checks.submit(("batch", k), sp)
+    got = checks.results(timeout=120.0)
+    assert set(got) == {("batch", k) for k in range(3)}
+    jobs = []
+    for k, sp in specs.items():
+        _, N, P1, psi = got[("batch", k)]
+        direct = bench.oracle_solve(sp)
+        assert direct[1] == N and np.array_equal(direct[3], psi)
+        j = Job(jid=k, n=sp["n"], seed=sp["seed"], nonlinear=sp["nonlinear"], T=sp["T"], s_kind=sp["s_kind"])
+        j.state = (psi * (1 + 1e-7 * (k + 1))).astype(np.complex64)
+        j.P1, j.steps = P1, N
+        jobs.append(j)
+    r = bench.oracle_errors(jobs, "batch", got)
+    assert r["checked"] == 3 and r["eligible"] == 3 and r["step_grids_equal"]
+    assert 2e-7 < r["max_state_err_vs_oracle"] < 1e-6
+    assert r["max_P1_err_vs_oracle"] < 1e-12

@@ -1,4 +1,5 @@
-"""T_s search (Sec. III.B) with batched GPU solves against the same search on oracle solves."""
+"""T_s search (Sec. III.B) with batched GPU solves against the same search on oracle solves
+(the XY algorithm from the sector ground state of H^xy on both sides, Sec. III.A.3)."""
 import pytest
 
 from instances import generate_ec3
@@ -35,7 +36,7 @@ def test_batched_Ts_matches_oracle(driver):
         psi0 = O.uniform_state(n)
     else:
         H = O.xy_hamiltonian(inst, driver="xy")
-        psi0 = O.dicke_state(n, bin(inst.solution).count("1"))
+        psi0 = O.xy_sector_ground_state(n, inst.clauses, bin(inst.solution).count("1"))[1]
 
     def E(Ts):
         out = []
