@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=1.0, help="requests per second (Poisson)")
     ap.add_argument("--serve-cap", type=float, default=120.0, help="time cap of the served stream (s)")
     ap.add_argument("--quick", action="store_true", help="small batched/served legs (not the stated workloads)")
+    ap.add_argument("--only-xy", action="store_true", help="run the XY-algorithm leg alone (profiling)")
+    ap.add_argument("--xy-n", type=int, default=24)
+    ap.add_argument("--xy-start", choices=["ground", "dicke"], default="ground",
+                    help="XY start: the sector ground state (Lanczos) or the Dicke state (no Lanczos workspace)")
     a = ap.parse_args()
     if a.quick:
         a.batch_count, a.serve_count, a.serve_cap = 48, 16, 30.0
@@ -384,9 +388,10 @@ def measure_batched(a, checks):
 def measure_serving(a):
     """The serving stream: `count` requests, Poisson arrivals at `rate`/s, n ~ U{10..26} with
     every 20th request n = 30, path linear/nonlinear uniform, T ~ U[10, 500], complex64;
-    continuous batching (n <= 20 in the batch, larger states on their own streams) under the
-    HBM budget, ended at the time cap (requests then unfinished are censored).  The same
-    requests then run one at a time under the same cap."""
+    continuous batching (n <= 16 in the batch; larger states, which fill the GPU alone, on their
+    own stream one at a time) under the HBM budget, arrived requests taken in order of estimated work; ended at
+    the time cap (requests then unfinished are censored).  The same requests then run one at a
+    time in the same order (the arrived request of least work next) under the same cap."""
     import copy
 
     from paper_1311_3938_gb300 import workloads as W
@@ -397,7 +402,12 @@ def measure_serving(a):
     seq_jobs = copy.deepcopy(jobs)
     for j in seq_jobs:
         j.keep = False
-    srv = W.Server(batch_max_n=20, max_members=128, steps_per_round=16, big_chunk=32)
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    large_grid = (3 * sms) // 4
+    srv = W.Server(batch_max_n=16, max_members=128, steps_per_round=16, big_chunk=32, policy="shortest", max_large=1,
+                   large_grid=large_grid)
     try:
         res = srv.serve(jobs, time_limit=a.serve_cap)
     finally:
@@ -409,7 +419,7 @@ def measure_serving(a):
     lat = [j.latency if not math.isnan(j.finished) else math.inf for j in offered]
     p50, c50 = quantile_censored(lat, 0.50)
     p99, c99 = quantile_censored(lat, 0.99)
-    s_done, s_cens, s_wall = W.serve_one_at_a_time(seq_jobs, time_limit=a.serve_cap)
+    s_done, s_cens, s_wall = W.serve_one_at_a_time(seq_jobs, time_limit=a.serve_cap, order="shortest")
     s_lat = [j.latency if not math.isnan(j.finished) else math.inf for j in seq_jobs if j.arrival <= a.serve_cap]
     sp50, sc50 = quantile_censored(s_lat, 0.50)
     sp99, sc99 = quantile_censored(s_lat, 0.99)
@@ -423,7 +433,10 @@ def measure_serving(a):
         "requests": len(jobs),
         "offered_within_cap": len(offered),
         "n_mix": {str(k): ns.count(k) for k in sorted(set(ns))},
+        "order": "arrived requests by estimated work T n 2^n, smallest first (both runs)",
         "served": {
+            "policy": f"continuous batching of n <= 16; one n > 16 state at a time on its own stream, its launches "
+                      f"capped at {large_grid} CTAs ({large_grid} of {sms} SMs) so that batch launches find SMs free",
             "completed": len(done),
             "censored_in_flight": len(cens),
             "wall_s": res["wall_s"],
@@ -437,6 +450,7 @@ def measure_serving(a):
             "by_route": res["by_route"],
         },
         "one_at_a_time": {
+            "policy": "one context at a time",
             "completed": len(s_done),
             "censored_in_flight": len(s_cens),
             "wall_s": s_wall,
@@ -452,7 +466,7 @@ def measure_serving(a):
     }
 
 
-def measure_xy(a, n=24, seed=3, pec=48):
+def measure_xy(a, seed=3, pec=48):
     """PEC step of the XY algorithm with the alpha = 8 catalyst (Eq. Hixy, Eq. nlpath), started
     from the ground state of H^xy in the solution's Hamming-weight sector (Lanczos, complex64):
     Y products run through the general-product loop, pairs across layouts through the remote
@@ -464,14 +478,22 @@ def measure_xy(a, n=24, seed=3, pec=48):
     from paper_1311_3938_gb300.engine import Context
     import paper_1311_3938_gb300 as P
 
+    n = a.xy_n
     inst = generate_ec3(n, seed)
     ctx = Context(n, P.AQC_C64)
     sched, k = HB.load_xy(ctx, inst, driver="xy", catalyst_alpha=8.0)
     ctx.set_schedule(20.0, sched)
     ctx.set_integrator(0, 0.0)
     t0 = time.perf_counter()
-    E0, resid, iters = HB.set_xy_ground_start(ctx, k)
+    if a.xy_start == "ground":
+        E0, resid, iters = HB.set_xy_ground_start(ctx, k)
+        start = f"ground state of H^xy in the weight-{k} sector"
+    else:
+        ctx.set_initial_state(("dicke", k))
+        E0, resid, iters = None, None, 0
+        start = f"Dicke state of weight {k}"
     t_ground = time.perf_counter() - t0
+    torch.cuda.empty_cache()  # the Lanczos basis is released before the timed steps
     ctx.propagate(4, stats=False)
     ms = []
     for _ in range(3):
@@ -481,8 +503,7 @@ def measure_xy(a, n=24, seed=3, pec=48):
     ctx.close()
     step_ms = min(ms)
     gbs = 7 * (1 << n) * 8 / (step_ms * 1e-3) / 1e9
-    return {"workload": f"XY algorithm + catalyst, EC3 n={n} seed {seed}, T=20, start: ground state of H^xy in the "
-                        f"weight-{k} sector, complex64",
+    return {"workload": f"XY algorithm + catalyst, EC3 n={n} seed {seed}, T=20, start: {start}, complex64",
             "ground_state": {"energy": E0, "residual": resid, "lanczos_steps": iters, "seconds": t_ground},
             "pec_step_ms": step_ms, "achieved": gbs, "unit": "GB/s (7 N b per PEC step)",
             "frac": gbs / peaks()[0]}
@@ -547,6 +568,16 @@ def measure_fp64_peak(device):
 
 
 # ----------------------------------------------------------------------------- our arm
+def run_xy_only(a):
+    import torch
+
+    import paper_1311_3938_gb300 as P
+
+    torch.cuda.set_device(0)
+    P.build()
+    print(json.dumps({"xy_algorithm": measure_xy(a)}), flush=True)
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -881,6 +912,8 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.only_xy:
+        run_xy_only(a)
     else:
         run_ours(a)
 

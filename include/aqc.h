@@ -236,6 +236,14 @@ int aqc_set_slab_bits(aqc_ctx *ctx, int slab_bits);
  * other k_steps; a failed capture returns AQC_E_CUDA from aqc_propagate. */
 int aqc_set_graph_steps(aqc_ctx *ctx, int k_steps);
 
+/* At most max_ctas CTAs for each layout pass of this context's evaluations (0 = no limit,
+ * the default: every SM).  The pass kernels are persistent over tiles, so a smaller grid only
+ * takes longer; results are unchanged (the state bit for bit, FP64 reductions up to their
+ * summation order).  A serving loop gives a large state that runs beside a batch of small ones
+ * part of the GPU, so that the batch's launches find SMs free instead of waiting for the large
+ * state's kernels to end.  AQC_E_INVAL for max_ctas < 0. */
+int aqc_set_grid_limit(aqc_ctx *ctx, int max_ctas);
+
 /* Graph replays (aqc_set_graph_steps) the context has issued since creation. */
 int aqc_get_graph_replays(const aqc_ctx *ctx, int64_t *out);
 

@@ -113,6 +113,7 @@ def lib():
             "aqc_tridiag_eigvec": (i32, [i32, C.POINTER(dbl), C.POINTER(dbl), dbl, C.POINTER(dbl)]),
             "aqc_launch_count": (i32, [vp, C.POINTER(i64)]),
             "aqc_set_graph_steps": (i32, [vp, i32]),
+            "aqc_set_grid_limit": (i32, [vp, i32]),
             "aqc_measure_fp64_fma": (i32, [i32, vp, i32, C.POINTER(dbl), C.POINTER(dbl)]),
             "aqc_get_graph_replays": (i32, [vp, C.POINTER(i64)]),
             "aqc_batch_workspace_bytes": (sz, [i32, i64]),
@@ -329,6 +330,10 @@ def aqc_tridiag_eigvec(a, b, lam):
 
 def aqc_set_graph_steps(ctx, k_steps):
     _check(ctx, lib().aqc_set_graph_steps(ctx, int(k_steps)))
+
+
+def aqc_set_grid_limit(ctx, max_ctas):
+    _check(ctx, lib().aqc_set_grid_limit(ctx, int(max_ctas)))
 
 
 def aqc_get_graph_replays(ctx):

@@ -196,6 +196,7 @@ struct aqc_ctx {
   // sequence): captured once on a private stream, replayed on `stream` after the host has
   // written the K steps' weights to d_wdev
   int graph_req = -1;             // 0 off, -1 automatic, K > 0 (a multiple of 4, <= kMaxGraphSteps)
+  int grid_limit = 0;             // > 0: CTAs per layout-pass launch at most (aqc_set_grid_limit)
   double* d_wdev = nullptr;       // 3 K weights of the replayed steps
   const double* cur_wdev = nullptr;  // set while a capture is issuing step j: d_wdev + 3 j
   cudaStream_t cap_stream = nullptr;
@@ -523,8 +524,17 @@ int build_tables(aqc_ctx* c) {
     };
     int k = np, nh = 0;
     if (l < nl) {
-      for (const DevFlip& f : per[l])
-        if (is_hop(f)) t->flips[pos + k++] = f;
+      // hops by class: which of the register-held tile bits (the pair bit of complex64 and the
+      // half bit) each flips, so that the kernels' hop loops know both at compile time
+      const uint32_t pair_bit = c->prec == AQC_C128 ? 0u : 1u, half_bit = c->prec == AQC_C128 ? 32u : 64u;
+      auto hop_class = [&](const DevFlip& f) {
+        return ((f.lx & pair_bit) ? 1 : 0) | ((f.lx & half_bit) ? 2 : 0);
+      };
+      for (int cls = 0; cls < 4; cls++) {
+        for (const DevFlip& f : per[l])
+          if (is_hop(f) && hop_class(f) == cls) t->flips[pos + k++] = f;
+        if (cls < 3) t->hop_class_end[l][cls] = k - np;
+      }
       nh = k - np;
       for (const DevFlip& f : per[l])
         if ((f.zm != 0 || f.has2) && !is_hop(f)) t->flips[pos + k++] = f;
@@ -596,6 +606,32 @@ int build_tables(aqc_ctx* c) {
     const int cnt = classes[k].end - classes[k].begin;
     const int maxv = classes[k].pen == AQC_PEN_SQUARED ? 4 * cnt : cnt;
     if (maxv <= 255) t->table_class = (int)k;
+  }
+  // a class whose clauses are the table class's minus a few (the catalyst H_{m-1} of Eq. nlpath
+  // beside H_f) counts as the cached byte minus those few clauses
+  if (t->table_class >= 0) {
+    const DevClass& B = classes[t->table_class];
+    int dp = cp;
+    for (size_t k = 0; k < classes.size(); k++) {
+      DevClass& C = classes[k];
+      if ((int)k == t->table_class || C.stepwise || C.pen != B.pen) continue;
+      std::vector<uint32_t> rest(t->clause_mask + B.begin, t->clause_mask + B.end);
+      bool sub = true;
+      for (int i = C.begin; i < C.end && sub; i++) {
+        auto it = std::find(rest.begin(), rest.end(), t->clause_mask[i]);
+        if (it == rest.end())
+          sub = false;
+        else
+          rest.erase(it);
+      }
+      if (!sub || (int)rest.size() > kMaxDerivedDiff || (int)rest.size() >= C.end - C.begin) continue;
+      if (dp + (int)rest.size() > kMaxClauses) break;
+      C.derived = 1;
+      C.dbegin = dp;
+      for (uint32_t m : rest) t->clause_mask[dp++] = m;
+      C.dend = dp;
+      t->classes[k] = C;
+    }
   }
   c->step_m = c->step_class >= 0 ? classes[c->step_class].end - classes[c->step_class].begin : 0;
   c->table_class = t->table_class;
@@ -715,6 +751,7 @@ ApplyParams base_params(aqc_ctx* c) {
   p.n = c->n;
   p.partials = c->d_partials;
   p.counter = c->d_counter;
+  p.max_grid = c->grid_limit;
   p.slots = c->d_slots;
   return p;
 }
@@ -758,6 +795,7 @@ int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, vo
         x.layout_index = l;
         for (int g = 0; g < 3; g++) x.w[g] = w[g];
         x.wdev = c->cur_wdev;
+        x.max_grid = c->grid_limit;
         x.qin = p.qin;
         x.qout = p.qout;
         x.ntiles = p.ntiles;
@@ -1483,6 +1521,15 @@ int aqc_measure_fp64_fma(int device, void* cuda_stream, int iters, double* tflop
   }
   *tflops_out = 2.0 * (double)fma64_count(blocks, iters) / ((double)ms * 1e-3) / 1e12;
   if (ms_out) *ms_out = ms;
+  return AQC_OK;
+}
+
+int aqc_set_grid_limit(aqc_ctx* ctx, int max_ctas) {
+  if (!ctx) return AQC_E_INVAL;
+  if (max_ctas < 0) FAIL(ctx, AQC_E_INVAL, "max_ctas must be >= 0");
+  ctx->grid_limit = max_ctas;
+  DeviceGuard dg(ctx->device);
+  drop_step_graph(ctx);  // captured launches carry the grid size
   return AQC_OK;
 }
 

@@ -43,9 +43,11 @@ struct DevClass {  // clauses [begin, end) share group, penalty and scale
   int32_t pen;     // 0 indicator [k != 1], 1 squared (1-k)^2
   int32_t begin, end;
   int32_t stepwise;  // the clause-by-clause sequence h_1..h_m (Eq. kpath), in order
-  int32_t pad;
+  int32_t derived;   // 1: the clauses are those of the byte-table class minus clause_mask[dbegin, dend)
+  int32_t dbegin, dend;
   double scale;
 };
+constexpr int kMaxDerivedDiff = 8;  // clauses a derived class may lack
 
 // Tile layout: tile bits are [0, c) and [h, h + w); t = c + w; remaining bits index tiles.
 // cb > 0: the tile belongs to a cluster of 2^cb CTAs; the top cb tile bits select the CTA, each
@@ -80,6 +82,10 @@ struct DevTables {
   int hop_count[kMaxLayouts + 2];   // leading entries of the general range that are hops:
                                     // X_iX_j + Y_iY_j with one real coefficient c, i.e.
                                     // 2c psi(z ^ x) where bits i, j of z differ, else 0
+  int hop_class_end[kMaxLayouts + 2][3];  // hops sorted by the register-held tile bits they
+                                    // flip (class 0: neither, 1: the pair bit, 2: the half
+                                    // bit, 3: both); ends of classes 0..2 within the hops'
+                                    // range, class 3 ends at hop_count
   int n_z;
   int n_classes;
   int table_class;                  // clause class whose counts are in the per-index byte table, or -1
@@ -112,6 +118,7 @@ struct ApplyParams {
   double w[3];       // group weights A, B, C at the evaluation time
   const double* wdev; // nullable: read the weights from this device array instead of w (steps
                       // replayed from a CUDA graph, whose weights the host writes before a replay)
+  int max_grid;       // > 0: at most this many CTAs (the kernels are persistent over tiles)
   double h;
   const uint8_t* dcode; // per-index clause counts of class table_class (nullable)
   const void* src;   // vector the Hamiltonian acts on
@@ -169,6 +176,7 @@ struct XPartialParams {
   int layout_index;
   double w[3];
   const double* wdev;    // nullable: weights from device memory (as ApplyParams::wdev)
+  int max_grid;          // > 0: at most this many CTAs
   const void* qin;       // nullable
   void* qout;
   uint32_t ntiles;

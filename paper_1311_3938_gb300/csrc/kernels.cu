@@ -18,6 +18,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "aqc_internal.h"
 
 namespace cg = cooperative_groups;
@@ -155,18 +157,22 @@ __device__ __forceinline__ R clause_sum_step(const DevTables* __restrict__ tab, 
   return sum;
 }
 
-template <typename R>
-__device__ __forceinline__ R clause_count(const DevTables* __restrict__ tab, const DevClass& cl, uint32_t z) {
+__device__ __forceinline__ int clause_range_count(const DevTables* __restrict__ tab, int pen, int b, int e, uint32_t z) {
   int cnt = 0;
-  if (cl.pen == 0) {
-    for (int k = cl.begin; k < cl.end; k++) cnt += (__popc(tab->clause_mask[k] & z) != 1);
+  if (pen == 0) {
+    for (int k = b; k < e; k++) cnt += (__popc(tab->clause_mask[k] & z) != 1);
   } else {
-    for (int k = cl.begin; k < cl.end; k++) {
+    for (int k = b; k < e; k++) {
       const int o = 1 - __popc(tab->clause_mask[k] & z);
       cnt += o * o;
     }
   }
-  return (R)cnt;
+  return cnt;
+}
+
+template <typename R>
+__device__ __forceinline__ R clause_count(const DevTables* __restrict__ tab, const DevClass& cl, uint32_t z) {
+  return (R)clause_range_count(tab, cl.pen, cl.begin, cl.end, z);
 }
 
 constexpr int kThreads = 256;
@@ -226,6 +232,7 @@ struct TileCtx {
   Layout L;
   uint32_t tsize, tmask;
   int np, npf, nh, ngl, ng, nz, ncls, tcls, stage;
+  int hc[3];  // ends of hop classes 0..2 (DevTables::hop_class_end)
   R dconst, wtab, h;
   // h/24 of the PEC corrector and predictor as a sum hi + lo of two state-precision numbers
   // (lo = 0 in FP64): every PEC step scales its increment by h/24, so a step size rounded once
@@ -274,6 +281,9 @@ __device__ __forceinline__ void load_coefficients(TileCtx<R>& T, const DevTables
   T.np = tab->plain_count[li];
   T.npf = tab->plain_fast[li];
   T.nh = tab->hop_count[li];
+  T.hc[0] = tab->hop_class_end[li][0];
+  T.hc[1] = tab->hop_class_end[li][1];
+  T.hc[2] = tab->hop_class_end[li][2];
   T.ngl = tab->flip_begin[li + 1] - fb - T.np;
   const int rb = tab->flip_begin[tab->n_layouts];
   const int nrem = with_remote ? tab->n_remote : 0;
@@ -432,8 +442,9 @@ __device__ __forceinline__ const C2* cluster_smem(const C2* s, uint32_t rank) {
 
 // HINT (L2 eviction priorities, full tiles only): 0 none; 1 a partial-sum pass whose source
 // tile and output are read again soon (kept), 2 a pass whose accesses are all last uses
-// (evicted first).
-template <typename R, int MODE, bool CL, int HINT = 0>
+// (evicted first).  HOPCLS: the hop loop by hop class (one loop per class, compile-time
+// register swaps and parities); off in the batched kernel, whose register budget it exceeds.
+template <typename R, int MODE, bool CL, int HINT = 0, bool HOPCLS = true>
 __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, uint32_t rank, R& rt0, R& rt1) {
   using C2 = typename Cplx<R>::T;
   constexpr int H = Blk<R>::H;
@@ -688,17 +699,63 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
       }
     }
     // 3a. hops X_iX_j + Y_iY_j: 2c psi(z ^ x) where the two bits of z differ (companion
-    //     coefficient c2 = -c after the i^2 phase, so cr - cr2 = 2c)
-    for (int kk = 0; kk < T.nh; kk++) {
-      const SFlip<R> f = T.s_gf[kk];
-      C2 u[G];
-      gather(f.lx, u);
-      const R c2 = f.cr - f.cr2;
+    //     coefficient c2 = -c after the i^2 phase, so cr - cr2 = 2c).  The thread's points
+    //     differ only in the register-held tile bits (pair bit HM, half bit HB), so within a hop
+    //     class (which of those bits the hop flips) the partners' register order and the points'
+    //     parities relative to point 0 are known at compile time: one parity per hop and thread,
+    //     and the coefficient is one of two values per point.
+    auto hop_class = [&](auto mh_tag, auto sw_tag, int k0, int k1) {
+      constexpr bool MH = decltype(mh_tag)::value, SW = decltype(sw_tag)::value;
+      for (int kk = k0; kk < k1; kk++) {
+        const SFlip<R> f = T.s_gf[kk];
+        const uint32_t hi = f.lx & tmask & ~(HM | HB);
+        C2 u[G];
+        if (hi == 0u) {  // the hop flips register-held bits only: partners are own points
 #pragma unroll
-      for (int g = 0; g < G; g++) {
-        const R c = (__popc(f.x & z[g]) & 1) ? c2 : (R)0;
-        ar[g] += c * u[g].x;
-        ai[g] += c * u[g].y;
+          for (int k = 0; k < 2; k++)
+#pragma unroll
+            for (int q = 0; q < H; q++) u[k * H + q] = own[(k ^ (SW ? 1 : 0)) * H + (q ^ (MH ? 1 : 0))];
+        } else {
+          C2 t0[H], t1[H];
+          ld16<C2, H>(s_p, (SW ? jh[1] : jh[0]) ^ hi, t0);
+          ld16<C2, H>(s_p, (SW ? jh[0] : jh[1]) ^ hi, t1);
+#pragma unroll
+          for (int q = 0; q < H; q++) {
+            u[q] = t0[q ^ (MH ? 1 : 0)];
+            u[H + q] = t1[q ^ (MH ? 1 : 0)];
+          }
+        }
+        const bool p0 = (__popc(f.x & z[0]) & 1) != 0;
+        const R c2 = f.cr - f.cr2;
+        const R cA = p0 ? c2 : (R)0, cB = p0 ? (R)0 : c2;  // parity of point 0, its opposite
+#pragma unroll
+        for (int k = 0; k < 2; k++)
+#pragma unroll
+          for (int q = 0; q < H; q++) {
+            const int g = k * H + q;
+            const R c = ((MH && q) != (SW && k)) ? cB : cA;
+            ar[g] += c * u[g].x;
+            ai[g] += c * u[g].y;
+          }
+      }
+    };
+    if (HOPCLS && full && !CL) {
+      hop_class(std::false_type{}, std::false_type{}, 0, T.hc[0]);
+      if (H == 2) hop_class(std::true_type{}, std::false_type{}, T.hc[0], T.hc[1]);
+      hop_class(std::false_type{}, std::true_type{}, T.hc[1], T.hc[2]);
+      if (H == 2) hop_class(std::true_type{}, std::true_type{}, T.hc[2], T.nh);
+    } else {
+      for (int kk = 0; kk < T.nh; kk++) {
+        const SFlip<R> f = T.s_gf[kk];
+        C2 u[G];
+        gather(f.lx, u);
+        const R c2 = f.cr - f.cr2;
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+          const R c = (__popc(f.x & z[g]) & 1) ? c2 : (R)0;
+          ar[g] += c * u[g].x;
+          ai[g] += c * u[g].y;
+        }
       }
     }
     // 3b. general products (Y/Z phases, complex coefficients) and remote products
@@ -742,8 +799,12 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
         for (int cc = 0; cc < T.ncls; cc++) {
           if (cc == T.tcls) continue;
           const DevClass cl = T.tab->classes[cc];
+          // a derived class: the cached count of the table class minus its few missing clauses
+          // (the same integer as counting every clause)
           const R cnt = cl.stepwise ? clause_sum_step<R>(T.tab, cl, z[g], T.step_k, T.step_wdone, T.step_wact)
-                                    : clause_count<R>(T.tab, cl, z[g]);
+                        : (cl.derived && T.tcls >= 0)
+                            ? (R)((int)code[g] - clause_range_count(T.tab, cl.pen, cl.dbegin, cl.dend, z[g]))
+                            : clause_count<R>(T.tab, cl, z[g]);
           d += (R)(cl.scale * pick3(T.w0, T.w1, T.w2, cl.group)) * cnt;
         }
         for (int k = 0; k < T.nz; k++) {
@@ -1094,10 +1155,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_batch(BatchLaunc
   T.acc = nullptr;
   R rt0 = (R)0, rt1 = (R)0;
   if (level > 0) {
-    process_tile<R, MODE_PARTIAL, false>(T, tile_base(T.L, it.tile), 0u, rt0, rt1);
+    process_tile<R, MODE_PARTIAL, false, 0, false>(T, tile_base(T.L, it.tile), 0u, rt0, rt1);
     return;
   }
-  process_tile<R, MODE_STEP, false>(T, tile_base(T.L, it.tile), 0u, rt0, rt1);
+  process_tile<R, MODE_STEP, false, 0, false>(T, tile_base(T.L, it.tile), 0u, rt0, rt1);
   double red[2] = {(double)rt0, (double)rt1};
   cta_reduce<2>(red, T.s_red);
   __shared__ int s_last;
@@ -1195,6 +1256,11 @@ static cudaError_t launch_one(const ApplyParams& p, int smem, cudaStream_t s) {
   int grid = 0;
   cudaError_t e = grid_for<R, MODE, CL>(p.ntiles, smem, s, &grid);
   if (e != cudaSuccess) return e;
+  if (p.max_grid > 0 && grid > p.max_grid) {  // whole clusters, at least one
+    const int unit = CL ? (1 << kClusterBits) : 1;
+    grid = p.max_grid / unit * unit;
+    if (grid < unit) grid = unit;
+  }
   if (CL) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "aqc_internal.h"
 
 namespace aqc {
@@ -90,16 +92,6 @@ __device__ __forceinline__ void fma4(float4& a, float c, const float4& g) {
   a.w = fmaf(c, g.w, a.w);
 }
 
-// per-pair coefficients: (c, c) for X strings; for hops c where the two bits of the output
-// index differ, else 0 (cm[r] bit 0 / bit 1: first / second amplitude of pair r qualifies)
-__device__ __forceinline__ void fma4m(float4& a, float c, uint32_t m, const float4& g) {
-  const float c0 = (m & 1u) ? c : 0.f, c1 = (m & 2u) ? c : 0.f;
-  a.x = fmaf(c0, g.x, a.x);
-  a.y = fmaf(c0, g.y, a.y);
-  a.z = fmaf(c1, g.z, a.z);
-  a.w = fmaf(c1, g.w, a.w);
-}
-
 __device__ __forceinline__ float4 swap_pair(const float4& g) { return make_float4(g.z, g.w, g.x, g.y); }
 
 // products flipping register positions only: acc[r] += c * own[r ^ RB]
@@ -120,20 +112,54 @@ __device__ __forceinline__ void smem_flip(float c, const unsigned char* row, flo
   }
 }
 
-// hops: the same with the per-pair masks of qualifying amplitudes
+// hops: 2c at output amplitudes whose two flipped bits differ, else 0.  The flip's register
+// bits (RB: local bits 6..8, the pair index r) and its pair bit (SW: local bit 0) fix the
+// parity of every amplitude of the thread relative to its first one: pair r's first amplitude
+// differs by parity(r & RB), its second by that ^ SW.  cA is the coefficient at the parity of
+// the thread's first amplitude, cB at the opposite parity, so no per-amplitude parity is left.
+template <int R_, int RB>
+__device__ __forceinline__ constexpr bool pair_parity() {
+  return (((R_ & RB) ^ ((R_ & RB) >> 1) ^ ((R_ & RB) >> 2)) & 1) != 0;
+}
+template <int RB, bool SW, int R_>
+__device__ __forceinline__ void hop_pair(float cA, float cB, const float4& g, float4& a) {
+  constexpr bool p = pair_parity<R_, RB>();
+  const float c0 = p ? cB : cA, c1 = (p != SW) ? cB : cA;
+  a.x = fmaf(c0, g.x, a.x);
+  a.y = fmaf(c0, g.y, a.y);
+  a.z = fmaf(c1, g.z, a.z);
+  a.w = fmaf(c1, g.w, a.w);
+}
 template <int RB, bool SW>
-__device__ __forceinline__ void smem_hop(float c, const unsigned char* row, const uint32_t (&cm)[8],
-                                         float4 (&acc)[8]) {
-#pragma unroll
-  for (int r = 0; r < 8; r++) {
+__device__ __forceinline__ void smem_hop(float cA, float cB, const unsigned char* row, float4 (&acc)[8]) {
+  auto one = [&](auto r_tag) {
+    constexpr int r = decltype(r_tag)::value;
     const float4 g = *reinterpret_cast<const float4*>(row + ((r ^ RB) << 9));
-    fma4m(acc[r], c, cm[r], SW ? swap_pair(g) : g);
-  }
+    hop_pair<RB, SW, r>(cA, cB, SW ? swap_pair(g) : g, acc[r]);
+  };
+  one(std::integral_constant<int, 0>{});
+  one(std::integral_constant<int, 1>{});
+  one(std::integral_constant<int, 2>{});
+  one(std::integral_constant<int, 3>{});
+  one(std::integral_constant<int, 4>{});
+  one(std::integral_constant<int, 5>{});
+  one(std::integral_constant<int, 6>{});
+  one(std::integral_constant<int, 7>{});
 }
 template <int RB>
-__device__ __forceinline__ void reg_hop(float c, const float4 (&own)[8], const uint32_t (&cm)[8], float4 (&acc)[8]) {
-#pragma unroll
-  for (int r = 0; r < 8; r++) fma4m(acc[r], c, cm[r], own[r ^ RB]);
+__device__ __forceinline__ void reg_hop(float cA, float cB, const float4 (&own)[8], float4 (&acc)[8]) {
+  auto one = [&](auto r_tag) {
+    constexpr int r = decltype(r_tag)::value;
+    hop_pair<RB, false, r>(cA, cB, own[r ^ RB], acc[r]);
+  };
+  one(std::integral_constant<int, 0>{});
+  one(std::integral_constant<int, 1>{});
+  one(std::integral_constant<int, 2>{});
+  one(std::integral_constant<int, 3>{});
+  one(std::integral_constant<int, 4>{});
+  one(std::integral_constant<int, 5>{});
+  one(std::integral_constant<int, 6>{});
+  one(std::integral_constant<int, 7>{});
 }
 
 __device__ __forceinline__ double weight_of(const XPartialParams& P, int g) {
@@ -196,6 +222,7 @@ __global__ void __launch_bounds__(kXThreads, 1) k_partial_x(const __grid_constan
   for (uint32_t tile = first; tile < ntiles; tile += stride, k++) {
     const int b = (int)(k & 1u);
     const uint32_t zb = tile_base(L, tile);
+    const uint32_t zj = zb | zoff[0];  // index of the thread's first amplitude
     float4 acc[8];
     if (qin) {
 #pragma unroll
@@ -216,44 +243,39 @@ __global__ void __launch_bounds__(kXThreads, 1) k_partial_x(const __grid_constan
     for (int kk = 0; kk < np; kk++) {
       const XFlip f = s_f[kk];
       const uint32_t rb = (f.lx & kXRegMask) >> 6, sx = f.lx & ~kXRegMask;
-      if (f.par) {  // hop: which output amplitudes have differing bits at the flip mask
-        uint32_t cm[8];
-        const uint32_t pb = __popc(zb & f.par) & 1u;
-#pragma unroll
-        for (int r = 0; r < 8; r++) {
-          const uint32_t p0 = pb ^ (__popc(zoff[r] & f.par) & 1u), p1 = p0 ^ (f.par & 1u);
-          cm[r] = p0 | (p1 << 1);
-        }
+      if (f.par) {  // hop: one parity per thread (its first amplitude), the rest is fixed by RB, SW
+        const bool pb = (__popc(zj & f.par) & 1u) != 0u;
+        const float cA = pb ? f.c : 0.f, cB = pb ? 0.f : f.c;
         if (sx == 0u) {
           switch (rb) {
-            case 1: reg_hop<1>(f.c, own, cm, acc); break;
-            case 2: reg_hop<2>(f.c, own, cm, acc); break;
-            case 3: reg_hop<3>(f.c, own, cm, acc); break;
-            case 4: reg_hop<4>(f.c, own, cm, acc); break;
-            case 5: reg_hop<5>(f.c, own, cm, acc); break;
-            case 6: reg_hop<6>(f.c, own, cm, acc); break;
-            default: reg_hop<7>(f.c, own, cm, acc); break;
+            case 1: reg_hop<1>(cA, cB, own, acc); break;
+            case 2: reg_hop<2>(cA, cB, own, acc); break;
+            case 3: reg_hop<3>(cA, cB, own, acc); break;
+            case 4: reg_hop<4>(cA, cB, own, acc); break;
+            case 5: reg_hop<5>(cA, cB, own, acc); break;
+            case 6: reg_hop<6>(cA, cB, own, acc); break;
+            default: reg_hop<7>(cA, cB, own, acc); break;
           }
         } else {
           const unsigned char* row = t + ((jw ^ (sx & ~1u)) << 3);
           const bool sw = (sx & 1u) != 0u;
           switch (rb | (sw ? 8u : 0u)) {
-            case 0: smem_hop<0, false>(f.c, row, cm, acc); break;
-            case 1: smem_hop<1, false>(f.c, row, cm, acc); break;
-            case 2: smem_hop<2, false>(f.c, row, cm, acc); break;
-            case 3: smem_hop<3, false>(f.c, row, cm, acc); break;
-            case 4: smem_hop<4, false>(f.c, row, cm, acc); break;
-            case 5: smem_hop<5, false>(f.c, row, cm, acc); break;
-            case 6: smem_hop<6, false>(f.c, row, cm, acc); break;
-            case 7: smem_hop<7, false>(f.c, row, cm, acc); break;
-            case 8: smem_hop<0, true>(f.c, row, cm, acc); break;
-            case 9: smem_hop<1, true>(f.c, row, cm, acc); break;
-            case 10: smem_hop<2, true>(f.c, row, cm, acc); break;
-            case 11: smem_hop<3, true>(f.c, row, cm, acc); break;
-            case 12: smem_hop<4, true>(f.c, row, cm, acc); break;
-            case 13: smem_hop<5, true>(f.c, row, cm, acc); break;
-            case 14: smem_hop<6, true>(f.c, row, cm, acc); break;
-            default: smem_hop<7, true>(f.c, row, cm, acc); break;
+            case 0: smem_hop<0, false>(cA, cB, row, acc); break;
+            case 1: smem_hop<1, false>(cA, cB, row, acc); break;
+            case 2: smem_hop<2, false>(cA, cB, row, acc); break;
+            case 3: smem_hop<3, false>(cA, cB, row, acc); break;
+            case 4: smem_hop<4, false>(cA, cB, row, acc); break;
+            case 5: smem_hop<5, false>(cA, cB, row, acc); break;
+            case 6: smem_hop<6, false>(cA, cB, row, acc); break;
+            case 7: smem_hop<7, false>(cA, cB, row, acc); break;
+            case 8: smem_hop<0, true>(cA, cB, row, acc); break;
+            case 9: smem_hop<1, true>(cA, cB, row, acc); break;
+            case 10: smem_hop<2, true>(cA, cB, row, acc); break;
+            case 11: smem_hop<3, true>(cA, cB, row, acc); break;
+            case 12: smem_hop<4, true>(cA, cB, row, acc); break;
+            case 13: smem_hop<5, true>(cA, cB, row, acc); break;
+            case 14: smem_hop<6, true>(cA, cB, row, acc); break;
+            default: smem_hop<7, true>(cA, cB, row, acc); break;
           }
         }
         continue;
@@ -337,6 +359,7 @@ cudaError_t launch_partial_x(const XPartialParams& p, int smem, cudaStream_t s) 
     cached_g = sms * (per < 1 ? 1 : per);
   }
   int g = cached_g;
+  if (p.max_grid > 0 && g > p.max_grid) g = p.max_grid;
   if ((uint32_t)g > p.ntiles) g = (int)p.ntiles;
   k_partial_x<<<g, kXThreads, smem, s>>>(p);
   return cudaGetLastError();

@@ -6,6 +6,7 @@ done by libaqc.so kernels.
 from __future__ import annotations
 
 import ctypes as C
+import warnings
 
 import numpy as np
 import torch
@@ -109,6 +110,10 @@ class Context:
         """PEC steps per CUDA-graph replay: 0 off, -1 automatic, or a multiple of 4 up to 64."""
         N.aqc_set_graph_steps(self.handle, k_steps)
 
+    def set_grid_limit(self, max_ctas=0):
+        """At most max_ctas CTAs per layout-pass launch (0: every SM)."""
+        N.aqc_set_grid_limit(self.handle, max_ctas)
+
     def graph_replays(self):
         return N.aqc_get_graph_replays(self.handle)
 
@@ -165,22 +170,32 @@ class Context:
         self._stage = stage  # the previous pair (if any) is released only now
         self._in_flight = []  # host tensors of enqueued copies (attach waited for the earlier ones)
 
+    @staticmethod
+    def _warn_pageable(host_tensor):
+        if torch.cuda.is_available() and not host_tensor.is_pinned():
+            warnings.warn("pageable host tensor: the staged copy cannot overlap the integration "
+                          "(use .pin_memory())", stacklevel=3)
+
     def stage_initial_state(self, host_tensor):
         """Enqueue the copy of a pinned host vector (qubit order) for the next
-        set_initial_state("staged"); returns at once."""
+        set_initial_state("staged"); returns at once.  The tensor stays referenced (and must not
+        change) until transfer_wait()."""
         if host_tensor.device.type != "cpu" or host_tensor.dtype != _torch_dtype(self.precision):
             raise ValueError("a host tensor of the state dtype is required")
         if host_tensor.numel() != self.N or not host_tensor.is_contiguous():
             raise ValueError("state has the wrong length or is not contiguous")
+        self._warn_pageable(host_tensor)
         N.aqc_stage_initial_state(self.handle, host_tensor.data_ptr())
         self._in_flight.append(host_tensor)  # alive until its copy is known to be done
 
     def fetch_state(self, host_tensor):
-        """Enqueue the copy of psi into a pinned host tensor; valid after transfer_wait()."""
+        """Enqueue the copy of psi into a pinned host tensor; valid after transfer_wait(), which
+        also releases the references the context keeps to the tensors of enqueued copies."""
         if host_tensor.device.type != "cpu" or host_tensor.dtype != _torch_dtype(self.precision):
             raise ValueError("a host tensor of the state dtype is required")
         if host_tensor.numel() != self.N or not host_tensor.is_contiguous():
             raise ValueError("state has the wrong length or is not contiguous")
+        self._warn_pageable(host_tensor)
         N.aqc_fetch_state(self.handle, host_tensor.data_ptr())
         self._in_flight.append(host_tensor)
 

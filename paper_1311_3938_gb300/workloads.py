@@ -236,25 +236,34 @@ def run_sweep_n20(seed=2, n=20, Ts=(10.0, 50.0, 200.0), device=0):
     return rows
 
 
-def serve_one_at_a_time(jobs, device=0, time_limit=None, chunk_amplitude_steps=1 << 26):
-    """The one-at-a-time baseline of a request stream: jobs in arrival order, each alone on the
-    GPU (one context), started when it has arrived and the previous one is done; propagated in
-    chunks of about `chunk_amplitude_steps` / 2^n grid steps so that a time limit ends the run
-    between chunks (the job then in progress is censored).  Returns (finished jobs, censored
-    jobs, wall seconds)."""
+def serve_one_at_a_time(jobs, device=0, time_limit=None, chunk_amplitude_steps=1 << 26, order="arrival"):
+    """The one-at-a-time baseline of a request stream: each job alone on the GPU (one context),
+    started once it has arrived and the previous one is done -- the next one in arrival order,
+    or (order "shortest") the arrived job of least work_estimate; propagated in chunks of about
+    `chunk_amplitude_steps` / 2^n grid steps so that a time limit ends the run between chunks
+    (the job then in progress is censored).  Returns (finished jobs, censored jobs, wall
+    seconds)."""
+    if order not in ("arrival", "shortest"):
+        raise ValueError("order must be 'arrival' or 'shortest'")
     pending = sorted(jobs, key=lambda j: j.arrival)
     done, censored = [], []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     now = lambda: time.perf_counter() - t0  # noqa: E731
-    for job in pending:
+    while pending:
         if time_limit and now() > time_limit:
             break
-        wait = job.arrival - now()
+        wait = pending[0].arrival - now()
         if wait > 0:
-            if time_limit and job.arrival > time_limit:
+            if time_limit and pending[0].arrival > time_limit:
                 break
             time.sleep(wait)
+        if order == "shortest":
+            t = now()
+            job = min((j for j in pending if j.arrival <= t), key=work_estimate)
+        else:
+            job = pending[0]
+        del pending[next(i for i, p in enumerate(pending) if p is job)]
         job.admitted = now()
         ctx, inst = make_context(job, device)
         chunk = max(16, chunk_amplitude_steps >> job.n)
@@ -440,12 +449,54 @@ def admit_ready(pending, now, used, budget, n_members, max_members, batch_max_n,
     return used
 
 
+def work_estimate(job):
+    """T n 2^n: a solve's grid steps (the step rule's N grows with T times the Hamiltonian's norm
+    bound, which grows with n) times its amplitudes, up to a constant; orders jobs by cost."""
+    return job.T * job.n * float(1 << job.n)
+
+
+def admit_shortest_first(pending, now, used, budget, n_members, max_members, batch_max_n, n_large, max_large,
+                         start):
+    """Admit arrived jobs of `pending` in order of work_estimate: a small job (n <= batch_max_n,
+    a batch member) while the batch has fewer than `max_members` members, a large one while fewer
+    than `max_large` large jobs run (`n_large()`); a job whose workspace does not fit the HBM
+    budget waits without blocking smaller jobs behind it.  Returns the new `used`."""
+    t = now()
+    arrived = sorted((j for j in pending if j.arrival <= t), key=work_estimate)
+    for job in arrived:
+        small = job.n <= batch_max_n
+        if small and n_members() >= max_members:
+            continue
+        if not small and n_large() >= max_large:
+            continue
+        need = job.workspace_bytes()
+        if used + need > budget:
+            continue
+        del pending[next(i for i, p in enumerate(pending) if p is job)]
+        used += need
+        start(job, small)
+    return used
+
+
 class Server:
-    """Continuous-batching request loop (see the module docstring)."""
+    """Continuous-batching request loop (see the module docstring).
+
+    policy "fifo": arrived jobs are admitted in arrival order as memory and the member limit
+    allow (admit_ready), every admitted large job runs at once.  policy "shortest": arrived jobs
+    are admitted in order of estimated work (admit_shortest_first) and at most `max_large` large
+    jobs run at a time; the large jobs' states are bandwidth-bound, so running several at once
+    adds no throughput and only delays each of them.  large_grid > 0 caps every launch of a
+    large job at that many CTAs (aqc_set_grid_limit): its persistent kernels would otherwise
+    hold every SM for their whole duration, and each batch launch would wait for one to end."""
 
     def __init__(self, precision=N.AQC_C64, device=0, hbm_budget=None, reserve=2 << 30, batch_max_n=22,
                  max_members=256, threads=256, steps_per_round=16, big_chunk=64, keep_state=False,
-                 big_first=False):
+                 big_first=False, policy="fifo", max_large=1, large_grid=0):
+        if policy not in ("fifo", "shortest"):
+            raise ValueError("policy must be 'fifo' or 'shortest'")
+        self.policy = policy
+        self.max_large = max_large
+        self.large_grid = large_grid  # CTA limit of a large job's launches (0: none; aqc_set_grid_limit)
         self.precision = precision
         self.device = device
         free, total = torch.cuda.mem_get_info(device)
@@ -492,10 +543,17 @@ class Server:
                 else:
                     stream = torch.cuda.Stream(self.device, priority=self.lo_prio)
                     ctx, inst = make_context(job, self.device, stream=stream)
+                    if self.large_grid:
+                        ctx.set_grid_limit(self.large_grid)
                     big.append([job, ctx, inst, stream, None, 0, []])
 
-            self.used = admit_ready(pending, now, self.used, self.budget, lambda: len(in_batch), self.max_members,
-                                    self.batch_max_n, start)
+            if self.policy == "fifo":
+                self.used = admit_ready(pending, now, self.used, self.budget, lambda: len(in_batch),
+                                        self.max_members, self.batch_max_n, start)
+            else:
+                self.used = admit_shortest_first(pending, now, self.used, self.budget, lambda: len(in_batch),
+                                                 self.max_members, self.batch_max_n, lambda: len(big),
+                                                 self.max_large, start)
             self.peak_used = max(self.peak_used, self.used)
             prof["admit_s"] += time.perf_counter() - ta
             self.occupancy.append(self.used / max(1, self.budget))

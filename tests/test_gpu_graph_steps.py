@@ -149,3 +149,17 @@ def test_not_used_under_step_control_and_bad_arguments():
     ctx.propagate(-1)
     assert ctx.graph_replays() == 0
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [C64, C128])
+def test_grid_limit_keeps_the_state(prec):
+    """aqc_set_grid_limit: every layout pass (the TMA-fed partial passes included) on a few CTAs;
+    the state is the same bit for bit, with and without graph replays (recaptured)."""
+    out = []
+    for limit in (0, 7, 1):
+        ctx, _ = _ec3_ctx(20, 4, prec, 0.3, nonlinear=True)
+        ctx.set_grid_limit(limit)
+        ctx.propagate(-1)
+        out.append(ctx.state())
+        ctx.close()
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])

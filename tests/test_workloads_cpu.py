@@ -1,6 +1,8 @@
 """Host-side logic of the workload drivers (no GPU)."""
 import math
 
+import pytest
+
 
 def test_random_jobs_seeded_and_poisson():
     from paper_1311_3938_gb300 import workloads as W
@@ -73,3 +75,39 @@ def test_admission_member_limit_blocks_the_queue():
     used, started = _admit(pending, 0.0, used, 1 << 40, members, max_members=2)
     assert started == [(2, True), (3, False)] and pending == []
     assert used == sum(x.workspace_bytes() for x in j)
+
+
+def test_admission_shortest_first_with_one_large_job():
+    """policy "shortest": arrived jobs by estimated work (T n 2^n); at most one large job runs;
+    a job that does not fit the budget waits without blocking smaller ones."""
+    from paper_1311_3938_gb300 import workloads as W
+
+    j = [_job(0, 24, 0.0), _job(1, 14, 0.0), _job(2, 22, 0.0), _job(3, 12, 0.0), _job(4, 12, 9.0)]
+    j[1].T, j[3].T = 50.0, 100.0  # 50 * 14 * 2^14 > 100 * 12 * 2^12
+    assert W.work_estimate(j[3]) < W.work_estimate(j[1]) < W.work_estimate(j[2]) < W.work_estimate(j[0])
+    pending = list(j)
+    started, members, large = [], [], []
+
+    def start(job, small):
+        started.append(job.jid)
+        (members if small else large).append(job.jid)
+
+    used = W.admit_shortest_first(pending, lambda: 1.0, 0, 1 << 40, lambda: len(members), 8, 20,
+                                  lambda: len(large), 1, start)
+    # small jobs by work, then the smaller of the two large ones; job 0 waits; job 4 not arrived
+    assert started == [3, 1, 2]
+    assert [x.jid for x in pending] == [0, 4]
+    assert used == sum(x.workspace_bytes() for x in (j[1], j[2], j[3]))
+    large.clear()
+    started.clear()
+    # budget too small for job 0: it waits, job 4 (arrived now, small) does not wait behind it
+    used = W.admit_shortest_first(pending, lambda: 10.0, 0, j[0].workspace_bytes() - 1, lambda: 0, 8, 20,
+                                  lambda: len(large), 1, start)
+    assert started == [4] and [x.jid for x in pending] == [0]
+
+
+def test_server_rejects_an_unknown_policy():
+    from paper_1311_3938_gb300 import workloads as W
+
+    with pytest.raises(ValueError):
+        W.serve_one_at_a_time([], order="random")
