@@ -107,10 +107,13 @@ typedef struct {
  * reduction slots.  Returns 0 for unsupported arguments. */
 size_t aqc_workspace_bytes(int n_qubits, int precision);
 
-/* The same with options: AQC_WS_STEP_CONTROL adds one state-sized vector (the state at the
- * start of a segment of constant step), which step-size control (aqc_set_integrator with
- * adaptive = 1) needs.  Returns 0 for unsupported arguments or unknown flags. */
+/* The same with options: AQC_WS_STEP_CONTROL adds one state-sized vector, which step-size
+ * control (aqc_set_integrator with adaptive = 1) uses for the state at the start of a segment of
+ * constant step, and y compensation (aqc_set_y_compensation) for the low part of y; the two are
+ * exclusive, so AQC_WS_Y_COMPENSATION names the same vector.  Returns 0 for unsupported
+ * arguments or unknown flags. */
 #define AQC_WS_STEP_CONTROL 1u
+#define AQC_WS_Y_COMPENSATION AQC_WS_STEP_CONTROL
 size_t aqc_workspace_bytes_ex(int n_qubits, int precision, unsigned flags);
 
 /* Create a context on `device` for n_qubits with state precision AQC_C128 or AQC_C64.
@@ -235,6 +238,17 @@ int aqc_set_slab_bits(aqc_ctx *ctx, int slab_bits);
  * one).  Grid steps that remain after the last whole replay run one by one.  AQC_E_INVAL for
  * other k_steps; a failed capture returns AQC_E_CUDA from aqc_propagate. */
 int aqc_set_graph_steps(aqc_ctx *ctx, int k_steps);
+
+/* Compensated corrector for complex64 states (reading of the FP32 state, Sec. I.B): each PEC
+ * step adds its increment h/24 (9 f_{n+1} + 19 f_n - 5 f_{n-1} + f_{n-2}) to y as an exact
+ * two-sum and keeps the rounding in a second complex64 vector (the workspace's extra vector,
+ * AQC_WS_Y_COMPENSATION), folded into the next step's sum.  The FP32 rounding of y then no
+ * longer accumulates over the run (about sqrt(steps) x 2^-24 without it); the step moves two
+ * more vectors (9 N b instead of 7 N b of algorithmic bytes).  The state, norms, fidelity and
+ * energy use y (within half an FP32 ulp of y + low part).  enable: 0 off (default) or 1; resets
+ * the integrator (set the initial state again).  AQC_E_UNSUPPORTED for complex128 or under
+ * step-size control, AQC_E_NOMEM without the extra vector. */
+int aqc_set_y_compensation(aqc_ctx *ctx, int enable);
 
 /* At most max_ctas CTAs for each layout pass of this context's evaluations (0 = no limit,
  * the default: every SM).  The pass kernels are persistent over tiles, so a smaller grid only

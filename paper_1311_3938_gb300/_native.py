@@ -24,6 +24,7 @@ AQC_E_TIMEOUT = -7
 AQC_UNIT_WEIGHTS = -1.0
 AQC_SEG_RUNNING, AQC_SEG_AT_T, AQC_SEG_REJECTED, AQC_SEG_GREW = 0, 1, 2, 3
 AQC_WS_STEP_CONTROL = 1
+AQC_WS_Y_COMPENSATION = AQC_WS_STEP_CONTROL
 
 AQC_C128 = 0
 AQC_C64 = 1
@@ -114,6 +115,7 @@ def lib():
             "aqc_launch_count": (i32, [vp, C.POINTER(i64)]),
             "aqc_set_graph_steps": (i32, [vp, i32]),
             "aqc_set_grid_limit": (i32, [vp, i32]),
+            "aqc_set_y_compensation": (i32, [vp, i32]),
             "aqc_measure_fp64_fma": (i32, [i32, vp, i32, C.POINTER(dbl), C.POINTER(dbl)]),
             "aqc_get_graph_replays": (i32, [vp, C.POINTER(i64)]),
             "aqc_batch_workspace_bytes": (sz, [i32, i64]),
@@ -330,6 +332,10 @@ def aqc_tridiag_eigvec(a, b, lam):
 
 def aqc_set_graph_steps(ctx, k_steps):
     _check(ctx, lib().aqc_set_graph_steps(ctx, int(k_steps)))
+
+
+def aqc_set_y_compensation(ctx, enable):
+    _check(ctx, lib().aqc_set_y_compensation(ctx, 1 if enable else 0))
 
 
 def aqc_set_grid_limit(ctx, max_ctas):

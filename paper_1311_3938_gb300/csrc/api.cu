@@ -187,7 +187,9 @@ struct aqc_ctx {
   int64_t rejects = 0;
   double max_err_acc = 0.0; // max estimate over accepted PEC steps
   double hmin = 0.0;
-  void* vec_save = nullptr; // state at the start of the current segment (AQC_WS_STEP_CONTROL)
+  void* vec_save = nullptr; // the workspace's extra vector (AQC_WS_STEP_CONTROL): the state at the
+                            // start of the current segment, or the low part of y under ycomp
+  int ycomp = 0;            // compensated complex64 corrector (aqc_set_y_compensation)
   int64_t seg_done0 = 0;    // accepted steps before the current segment
   std::vector<aqc_segment> segs;
   int64_t launches = 0;  // kernel launches issued (monotone counter)
@@ -440,12 +442,13 @@ int build_tables(aqc_ctx* c) {
       const std::vector<int> inv = inverse_perm(np);
       std::vector<int> m(c->n);
       for (int p = 0; p < c->n; p++) m[p] = old[inv[p]];
-      const int live[] = {V_Y, V_P, V_F0, V_F0 + 1, V_F0 + 2, V_F0 + 3};
-      for (int v : live) {
-        int rc = permute_gather(c, c->vec[V_ACC], c->vec[v], m);
+      void* live[] = {c->vec[V_Y], c->vec[V_P], c->vec[V_F0], c->vec[V_F0 + 1], c->vec[V_F0 + 2],
+                      c->vec[V_F0 + 3], c->vec_save};
+      for (void* v : live) {
+        if (!v) continue;
+        int rc = permute_gather(c, c->vec[V_ACC], v, m);
         if (rc) return rc;
-        CUDA_TRY(c, cudaMemcpyAsync(c->vec[v], c->vec[V_ACC], (size_t)c->N * c->amp, cudaMemcpyDeviceToDevice,
-                                    c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(v, c->vec[V_ACC], (size_t)c->N * c->amp, cudaMemcpyDeviceToDevice, c->stream));
       }
     }
     c->perm = np;
@@ -857,6 +860,8 @@ int start_history(aqc_ctx* c) {
   CUDA_TRY(c, launch_predict(c->prec, c->vec[V_P], c->vec[V_Y], c->vec[V_F0 + 3], c->vec[V_F0 + 2],
                              c->vec[V_F0 + 1], c->vec[V_F0 + 0], c->h, c->N, c->stream));
   c->launches++;
+  if (c->ycomp)  // the PEC steps' low part of y starts at zero
+    CUDA_TRY(c, cudaMemsetAsync(c->vec_save, 0, (size_t)c->N * c->amp, c->stream));
   c->hist_ready = true;
   return AQC_OK;
 }
@@ -913,7 +918,8 @@ int pec_step(aqc_ctx* c) {
   fin.pout = c->vec[V_P];
   // under step-size control y_{n+1} goes to the scratch vector, so a rejected step keeps y_n
   fin.yout = c->adaptive ? c->vec[V_ACC] : nullptr;
-  int rc = c->slab.n_slabs ? pec_step_slabs(c, w, fin) : evaluate(c, w, c->vec[V_P], fin, nullptr);
+  fin.ylo = c->ycomp ? c->vec_save : nullptr;
+  int rc = (c->slab.n_slabs && !c->ycomp) ? pec_step_slabs(c, w, fin) : evaluate(c, w, c->vec[V_P], fin, nullptr);
   if (rc) return rc;
   c->evals++;
   return AQC_OK;  // the caller counts the step (count_step) or decides on it (control_step)
@@ -1524,6 +1530,21 @@ int aqc_measure_fp64_fma(int device, void* cuda_stream, int iters, double* tflop
   return AQC_OK;
 }
 
+int aqc_set_y_compensation(aqc_ctx* ctx, int enable) {
+  if (!ctx) return AQC_E_INVAL;
+  if (enable) {
+    if (ctx->prec != AQC_C64) FAIL(ctx, AQC_E_UNSUPPORTED, "y compensation is for complex64 states");
+    if (!ctx->vec_save)
+      FAIL(ctx, AQC_E_NOMEM, "y compensation needs the workspace's extra vector (AQC_WS_Y_COMPENSATION)");
+    if (ctx->adaptive) FAIL(ctx, AQC_E_UNSUPPORTED, "y compensation and step-size control are exclusive");
+  }
+  ctx->ycomp = enable ? 1 : 0;
+  ctx->have_state = false;  // the integrator restarts from a new initial state
+  DeviceGuard dg(ctx->device);
+  drop_step_graph(ctx);
+  return AQC_OK;
+}
+
 int aqc_set_grid_limit(aqc_ctx* ctx, int max_ctas) {
   if (!ctx) return AQC_E_INVAL;
   if (max_ctas < 0) FAIL(ctx, AQC_E_INVAL, "max_ctas must be >= 0");
@@ -1554,6 +1575,7 @@ int aqc_set_integrator(aqc_ctx* ctx, int64_t n_steps, double kappa, int adaptive
   if (adaptive != 0 && adaptive != 1) FAIL(ctx, AQC_E_INVAL, "adaptive must be 0 or 1");
   if (adaptive && !(tol > 0.0 && isfinite(tol))) FAIL(ctx, AQC_E_INVAL, "tol must be positive and finite");
   if (adaptive && ctx->in_batch) FAIL(ctx, AQC_E_STATE, "a batch member cannot take step-size control");
+  if (adaptive && ctx->ycomp) FAIL(ctx, AQC_E_UNSUPPORTED, "step-size control and y compensation are exclusive");
   if (adaptive && !ctx->vec_save)
     FAIL(ctx, AQC_E_NOMEM, "the workspace has no room for step-size control (aqc_workspace_bytes_ex with "
                            "AQC_WS_STEP_CONTROL)");
@@ -2111,6 +2133,7 @@ int aqc_batch_add(aqc_batch* b, aqc_ctx* c, int* slot_out) {
   for (const ClauseH& k : c->clauses)
     if (k.stepwise) BFAIL(b, AQC_E_UNSUPPORTED, "clause-by-clause sequences are not batched");
   if (c->adaptive) BFAIL(b, AQC_E_UNSUPPORTED, "contexts under step-size control are not batched");
+  if (c->ycomp) BFAIL(b, AQC_E_UNSUPPORTED, "contexts under y compensation are not batched");
   for (aqc_ctx* m : b->members)
     if (m == c) BFAIL(b, AQC_E_INVAL, "context is already a member");
   int slot = -1;

@@ -133,6 +133,7 @@ struct ApplyParams {
   void* fout;        // STEP: f_{n+1};  DERIV: f;  RK4 stage 1: history f_n
   void* pout;        // STEP: p_{n+2};  RK4: stage input for the next stage (ys)
   void* acc;         // RK4 accumulator
+  void* ylo;         // STEP, complex64: low part of y (compensated corrector; nullable)
   int step_k;        // clause-by-clause segment k (0: no clause of the sequence active)
   double step_wdone; // coefficient of clauses j < k of the sequence
   double step_wact;  // coefficient of clause k

@@ -245,6 +245,7 @@ struct TileCtx {
   double w0, w1, w2;
   const C2 *src, *qin, *f0, *f1, *f2;
   C2 *qout, *y, *yout, *fout, *pout, *acc;
+  C2* ylo;  // STEP, FP32: low part of y (compensated corrector), nullable
   C2* s_p;
   uint8_t* s_code;
   PFlip<R>* s_pf;
@@ -440,11 +441,24 @@ __device__ __forceinline__ const C2* cluster_smem(const C2* s, uint32_t rank) {
   return cg::this_cluster().map_shared_rank(s, rank);
 }
 
+// hi + lo + inc with the sum of hi and inc taken exactly (two-sum) and folded into lo; returns
+// the new hi and leaves the new lo in `lo` (|lo| <= half an ulp of hi)
+__device__ __forceinline__ float comp_add(float hi, float& lo, float inc) {
+  const float s = hi + inc;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (inc - bp);
+  const float l = lo + e;
+  const float h = s + l;
+  lo = l - (h - s);
+  return h;
+}
+__device__ __forceinline__ double comp_add(double hi, double& lo, double inc) { return hi + inc; }
+
 // HINT (L2 eviction priorities, full tiles only): 0 none; 1 a partial-sum pass whose source
 // tile and output are read again soon (kept), 2 a pass whose accesses are all last uses
 // (evicted first).  HOPCLS: the hop loop by hop class (one loop per class, compile-time
 // register swaps and parities); off in the batched kernel, whose register budget it exceeds.
-template <typename R, int MODE, bool CL, int HINT = 0, bool HOPCLS = true>
+template <typename R, int MODE, bool CL, int HINT = 0, bool HOPCLS = true, bool COMP = false>
 __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, uint32_t rank, R& rt0, R& rt1) {
   using C2 = typename Cplx<R>::T;
   constexpr int H = Blk<R>::H;
@@ -453,6 +467,7 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
   constexpr uint32_t HB = 32 * H;
   constexpr bool kNeedY = (MODE == MODE_STEP || MODE == MODE_RK4);
   constexpr bool kNeedF = (MODE == MODE_STEP);
+  constexpr bool kComp = (COMP && MODE == MODE_STEP && sizeof(R) == 4);  // FP32 corrector carries y's low part
   const C2 zero2 = C2{(R)0, (R)0};
   const Layout L = T.L;
   const uint32_t tsize = T.tsize, tmask = T.tmask;
@@ -539,6 +554,11 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
     }
     // 1. pointwise global loads first; they complete while the shared-memory gathers run
     C2 qv[G], y0[G], a[G], b[G], c[G];
+    C2 yl[G];  // low part of y (compensated FP32 corrector, COMP)
+    if (kComp) {
+#pragma unroll
+      for (int g = 0; g < G; g++) yl[g] = zero2;
+    }
     uint32_t code[G];
     if (full) {
 #pragma unroll
@@ -560,6 +580,11 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
           gld16<C2, H, HINT>(T.y, zh[k], t, T.pol_drop);
 #pragma unroll
           for (int q = 0; q < H; q++) y0[k * H + q] = t[q];
+        }
+        if (kComp) {
+          gld16<C2, H, HINT>(T.ylo, zh[k], t, T.pol_drop);
+#pragma unroll
+          for (int q = 0; q < H; q++) yl[k * H + q] = t[q];
         }
         if (kNeedF) {
           gld16<C2, H, HINT>(T.f0, zh[k], t, T.pol_drop);
@@ -584,6 +609,7 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
       for (int g = 0; g < G; g++) {
         qv[g] = (T.qin && ok[g]) ? __ldcg(T.qin + z[g]) : zero2;
         if (kNeedY) y0[g] = ok[g] ? T.y[z[g]] : zero2;
+        if (kComp) yl[g] = ok[g] ? T.ylo[z[g]] : zero2;
         if (kNeedF) {
           a[g] = ok[g] ? T.f0[z[g]] : zero2;
           b[g] = ok[g] ? T.f1[z[g]] : zero2;
@@ -858,8 +884,16 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
           // the weighted sums times (hi + lo): h24 * S + h24lo * S with one rounding of the sum
           const R scx = (R)9 * fn.x + (R)19 * a[g].x - (R)5 * b[g].x + c[g].x;
           const R scy = (R)9 * fn.y + (R)19 * a[g].y - (R)5 * b[g].y + c[g].y;
-          yn.x = y0[g].x + fma(h24, scx, h24lo * scx);
-          yn.y = y0[g].y + fma(h24, scy, h24lo * scy);
+          const R ix = fma(h24, scx, h24lo * scx), iy = fma(h24, scy, h24lo * scy);
+          if (kComp) {
+            // compensated: (y + y_lo) + increment as an exact two-sum, renormalised, so the
+            // rounding of y does not accumulate over the run
+            yn.x = comp_add(y0[g].x, yl[g].x, ix);
+            yn.y = comp_add(y0[g].y, yl[g].y, iy);
+          } else {
+            yn.x = y0[g].x + ix;
+            yn.y = y0[g].y + iy;
+          }
           const R spx = (R)55 * fn.x - (R)59 * a[g].x + (R)37 * b[g].x - (R)9 * c[g].x;
           const R spy = (R)55 * fn.y - (R)59 * a[g].y + (R)37 * b[g].y - (R)9 * c[g].y;
           pn.x = yn.x + fma(h24, spx, h24lo * spx);
@@ -901,6 +935,7 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
     C2* d1 = MODE == MODE_PARTIAL ? T.qout : (MODE == MODE_DERIV ? T.fout : (MODE == MODE_STEP ? T.yout : nullptr));
     C2* d2 = MODE == MODE_STEP ? T.fout : nullptr;
     C2* d3 = MODE == MODE_STEP ? T.pout : nullptr;
+    C2* d4 = kComp ? T.ylo : nullptr;
     if (MODE == MODE_RK4) {
       d1 = T.stage == 1 ? T.fout : (T.stage == 4 ? T.y : nullptr);
       d2 = T.stage <= 3 ? T.acc : nullptr;
@@ -913,6 +948,7 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
         if (d1) gst16<C2, H, HINT>(d1, zh[k], o1 + k * H, pol);
         if (d2) gst16<C2, H, HINT>(d2, zh[k], o2 + k * H, pol);
         if (d3) gst16<C2, H, HINT>(d3, zh[k], o3 + k * H, pol);
+        if (kComp && d4) gst16<C2, H, HINT>(d4, zh[k], yl + k * H, pol);
       }
     } else {
 #pragma unroll
@@ -921,12 +957,13 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
         if (d1) d1[z[g]] = o1[g];
         if (d2) d2[z[g]] = o2[g];
         if (d3) d3[z[g]] = o3[g];
+        if (kComp && d4) d4[z[g]] = yl[g];
       }
     }
   }
 }
 
-template <typename R, int MODE, bool CL>
+template <typename R, int MODE, bool CL, bool COMP = false>
 __global__ void __launch_bounds__(kThreads, (MODE == MODE_PARTIAL && sizeof(R) == 4 && !CL) ? 3 : 2)
     k_apply(const ApplyParams P) {
   using C2 = typename Cplx<R>::T;
@@ -951,6 +988,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_PARTIAL && sizeof(R) =
   T.fout = reinterpret_cast<C2*>(P.fout);
   T.pout = reinterpret_cast<C2*>(P.pout);
   T.acc = reinterpret_cast<C2*>(P.acc);
+  T.ylo = reinterpret_cast<C2*>(P.ylo);
 
   // reductions: per-thread partials over one tile in the state precision (a few dozen
   // points), promoted to FP64 once per tile; FP64 across tiles, CTAs and the grid
@@ -966,7 +1004,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_PARTIAL && sizeof(R) =
   }
   for (uint32_t tile = first; tile < P.ntiles; tile += stride) {
     R rt0 = (R)0, rt1 = (R)0;
-    process_tile<R, MODE, CL>(T, tile_base(T.L, tile), rank, rt0, rt1);
+    process_tile<R, MODE, CL, 0, true, COMP>(T, tile_base(T.L, tile), rank, rt0, rt1);
     red[0] += (double)rt0;
     red[1] += (double)rt1;
   }
@@ -1052,6 +1090,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_slab(const SlabParams S) {
   TS.pout = reinterpret_cast<C2*>(A.pout);
   TS.qout = nullptr;
   TS.acc = nullptr;
+  TS.ylo = TP.ylo = nullptr;  // the slab order is not used under y compensation
   TP.qin = reinterpret_cast<const C2*>(B.qin);
   TP.qout = reinterpret_cast<C2*>(B.qout);
   TP.y = TP.yout = nullptr;
@@ -1153,6 +1192,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_batch(BatchLaunc
   T.fout = v[kVecF0 + (int)((n + 1) & 3)];
   T.pout = v[kVecP];
   T.acc = nullptr;
+  T.ylo = nullptr;  // members run the plain corrector (aqc_batch_add refuses y compensation)
   R rt0 = (R)0, rt1 = (R)0;
   if (level > 0) {
     process_tile<R, MODE_PARTIAL, false, 0, false>(T, tile_base(T.L, it.tile), 0u, rt0, rt1);
@@ -1196,10 +1236,10 @@ size_t apply_smem_bytes(int prec, int t, int n_plain, int n_general, int n_z) {
 
 // Persistent grid: (resident CTAs per SM for this smem size) x SMs, at most one CTA per tile;
 // for cluster layouts, the number of clusters that can be resident at once (x cluster size).
-template <typename R, int MODE, bool CL>
+template <typename R, int MODE, bool CL, bool COMP>
 static cudaError_t grid_for(uint32_t ntiles, int smem, cudaStream_t s, int* grid) {
   static int configured = 0, cached_smem = -1, cached_dev = -1, cached_g = 0;
-  auto kern = k_apply<R, MODE, CL>;
+  auto kern = k_apply<R, MODE, CL, COMP>;
   if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -1251,10 +1291,10 @@ static cudaError_t grid_for(uint32_t ntiles, int smem, cudaStream_t s, int* grid
   return cudaSuccess;
 }
 
-template <typename R, int MODE, bool CL>
+template <typename R, int MODE, bool CL, bool COMP = false>
 static cudaError_t launch_one(const ApplyParams& p, int smem, cudaStream_t s) {
   int grid = 0;
-  cudaError_t e = grid_for<R, MODE, CL>(p.ntiles, smem, s, &grid);
+  cudaError_t e = grid_for<R, MODE, CL, COMP>(p.ntiles, smem, s, &grid);
   if (e != cudaSuccess) return e;
   if (p.max_grid > 0 && grid > p.max_grid) {  // whole clusters, at least one
     const int unit = CL ? (1 << kClusterBits) : 1;
@@ -1274,10 +1314,10 @@ static cudaError_t launch_one(const ApplyParams& p, int smem, cudaStream_t s) {
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_apply<R, MODE, CL>, p);
+    e = cudaLaunchKernelEx(&cfg, k_apply<R, MODE, CL, COMP>, p);
     if (e != cudaSuccess) return e;
   } else {
-    k_apply<R, MODE, CL><<<grid, kThreads, smem, s>>>(p);
+    k_apply<R, MODE, CL, COMP><<<grid, kThreads, smem, s>>>(p);
   }
   return cudaGetLastError();
 }
@@ -1286,7 +1326,14 @@ template <typename R, bool CL>
 static cudaError_t launch_prec(const ApplyParams& p, int smem, cudaStream_t s) {
   switch (p.mode) {
     case MODE_PARTIAL: return launch_one<R, MODE_PARTIAL, CL>(p, smem, s);
-    case MODE_STEP: return launch_one<R, MODE_STEP, CL>(p, smem, s);
+    case MODE_STEP:
+      // the compensated corrector (complex64, per-CTA tiles) is an instantiation of its own
+      if constexpr (sizeof(R) == 4 && !CL) {
+        if (p.ylo) return launch_one<R, MODE_STEP, CL, true>(p, smem, s);
+      } else {
+        if (p.ylo) return cudaErrorInvalidValue;
+      }
+      return launch_one<R, MODE_STEP, CL>(p, smem, s);
     case MODE_RK4: return launch_one<R, MODE_RK4, CL>(p, smem, s);
     case MODE_DERIV: return launch_one<R, MODE_DERIV, CL>(p, smem, s);
     case MODE_ENERGY: return launch_one<R, MODE_ENERGY, CL>(p, smem, s);

@@ -25,9 +25,13 @@ def _torch_dtype(precision):
 class Context:
     """One state vector of n qubits on one GPU with its integrator (include/aqc.h)."""
 
-    def __init__(self, n: int, precision: int = N.AQC_C128, device: int = 0, stream=None, step_control=False):
-        """step_control=True reserves the workspace vector that step-size control needs
-        (set_integrator(adaptive=True))."""
+    def __init__(self, n: int, precision: int = N.AQC_C128, device: int = 0, stream=None, step_control=False,
+                 extra_vector=None):
+        """step_control=True (or extra_vector=True) reserves the workspace's extra vector, which
+        step-size control (set_integrator(adaptive=True)) or y compensation
+        (set_y_compensation()) uses."""
+        if extra_vector is not None:
+            step_control = step_control or bool(extra_vector)
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
         self.n = n
@@ -109,6 +113,10 @@ class Context:
     def set_graph_steps(self, k_steps=-1):
         """PEC steps per CUDA-graph replay: 0 off, -1 automatic, or a multiple of 4 up to 64."""
         N.aqc_set_graph_steps(self.handle, k_steps)
+
+    def set_y_compensation(self, enable=True):
+        """Compensated complex64 corrector (aqc_set_y_compensation); set the initial state after."""
+        N.aqc_set_y_compensation(self.handle, enable)
 
     def set_grid_limit(self, max_ctas=0):
         """At most max_ctas CTAs per layout-pass launch (0: every SM)."""

@@ -163,3 +163,51 @@ def test_grid_limit_keeps_the_state(prec):
         out.append(ctx.state())
         ctx.close()
     assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
+def test_compensated_corrector_replays_and_arguments():
+    """y compensation: graph replays give the same bits as single steps; the state differs from
+    the plain corrector's by rounding only; complex128, a missing extra vector, step-size
+    control and batches are refused."""
+    from paper_1311_3938_gb300 import _native as N
+    from paper_1311_3938_gb300 import hamiltonians as HB
+    from paper_1311_3938_gb300.engine import Batch, Context
+
+    inst = generate_ec3(14, 5)
+    out = {}
+    for comp, k in ((False, 0), (True, 0), (True, 8)):
+        ctx = Context(14, C64, extra_vector=True)
+        ctx.set_graph_steps(k)
+        HB.load_ec3(ctx, inst, pairs=xx_pairs(14, 5))
+        ctx.set_schedule(4.0, HB.nonlinear_schedule(), 1)
+        ctx.set_integrator(0, 0.0)
+        ctx.set_y_compensation(comp)
+        ctx.set_initial_state("uniform")
+        ctx.propagate(-1)
+        out[(comp, k)] = (ctx.state(), ctx.graph_replays())
+        ctx.close()
+    assert np.array_equal(out[(True, 0)][0], out[(True, 8)][0]) and out[(True, 8)][1] > 0
+    assert 0 < rel_err(out[(True, 0)][0], out[(False, 0)][0]) < 1e-5
+    with Context(8, C128, extra_vector=True) as c:
+        with pytest.raises(N.AqcError) as e:
+            c.set_y_compensation(True)
+        assert e.value.code == N.AQC_E_UNSUPPORTED
+    with Context(8, C64) as c:
+        with pytest.raises(N.AqcError) as e:
+            c.set_y_compensation(True)
+        assert e.value.code == N.AQC_E_NOMEM
+    c = Context(8, C64, extra_vector=True)
+    c.set_y_compensation(True)
+    with pytest.raises(N.AqcError) as e:
+        c.set_integrator(0, 0.0, adaptive=True, tol=1e-6)
+    assert e.value.code == N.AQC_E_UNSUPPORTED
+    HB.load_ec3(c, generate_ec3(8, 1))
+    c.set_schedule(1.0, HB.linear_schedule())
+    c.set_integrator(0, 0.0)
+    c.set_initial_state("uniform")
+    b = Batch(C64, max_members=2, max_items=64)
+    with pytest.raises(N.AqcError) as e:
+        b.add(c)
+    assert e.value.code == N.AQC_E_UNSUPPORTED
+    b.close()
+    c.close()

@@ -9,7 +9,9 @@
   the TMA-fed partial passes, the clause byte cache and the fused PEC kernel as the bench runs them.
 
 Each case is compared on the whole state vector, in both precisions (relative error <= 1e-10
-for complex128, <= 1e-5 for complex64).  The oracle solves run in worker threads (the C oracle
+for complex128, <= 1e-5 for complex64).  The complex64 long run and one n = 20 solve also run
+with the compensated corrector (aqc_set_y_compensation), whose error must stay far below the
+uncompensated one's.  The oracle solves run in worker threads (the C oracle
 releases the GIL): the long single-threaded run beside a queue of multithreaded ones, all
 started when the module's first test asks for them, so they overlap the GPU solves.
 """
@@ -78,16 +80,18 @@ def oracle_runs():
         ex.shutdown(wait=True, cancel_futures=True)
 
 
-def _gpu_solve(n, seed, T, nonlinear, s_kind, prec, max_steps=-1):
+def _gpu_solve(n, seed, T, nonlinear, s_kind, prec, max_steps=-1, ycomp=False):
     from paper_1311_3938_gb300 import hamiltonians as HB
     from paper_1311_3938_gb300.engine import Context
 
     inst = generate_ec3(n, seed)
     pairs = xx_pairs(n, seed) if nonlinear else None
-    ctx = Context(n, prec)
+    ctx = Context(n, prec, extra_vector=ycomp)
     HB.load_ec3(ctx, inst, pairs=pairs)
     ctx.set_schedule(T, HB.nonlinear_schedule() if nonlinear else HB.linear_schedule(), s_kind)
     ctx.set_integrator(0, 0.0)
+    if ycomp:
+        ctx.set_y_compensation(True)
     ctx.set_initial_state("uniform")
     st = ctx.propagate(max_steps)
     psi = ctx.state()
@@ -148,3 +152,23 @@ def test_n28_first_steps_full_state(prec, oracle_runs):
     del psi
     print(f"n=28: precision {prec}, first {N28['steps']} steps, relative state error {err:.3e}")
     assert err < TOL_STATE[prec], (prec, err)
+
+
+def test_long_runtime_compensated_corrector(oracle_runs):
+    """The 42 000-step run in complex64 with y compensation: the rounding of y no longer
+    accumulates, so the state error falls well below the plain FP32 corrector's (5e-6)."""
+    st, psi, P1, inst = _gpu_solve(**LONG, prec=C64, ycomp=True)
+    N, ref = oracle_runs["long"].result()
+    err = rel_err(psi, ref.psi)
+    print(f"long runtime, compensated complex64: {N} steps, relative state error {err:.3e}")
+    assert st["steps_done"] == N
+    assert err < 1.5e-6, err
+
+
+def test_n20_compensated_corrector(oracle_runs):
+    """The n = 20 nonlinear smoothstep solve (three layout passes per step) with y compensation."""
+    st, psi, P1, inst = _gpu_solve(20, 2, 10.0, True, 1, C64, ycomp=True)
+    N, ref = oracle_runs[("n20", True, 1)].result()
+    err = rel_err(psi, ref.psi)
+    print(f"n=20 compensated complex64: {N} steps, relative state error {err:.3e}")
+    assert err < TOL_STATE[C64], err
