@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-xy", action="store_true")
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-ycomp", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-count", type=int, default=40)
@@ -509,10 +510,43 @@ def measure_xy(a, seed=3, pec=48):
             "frac": gbs / peaks()[0]}
 
 
+def measure_ycomp(a, pec=48):
+    """The headline PEC step (EC3 n, seed 3, linear, T = 100, complex64) with the compensated
+    corrector (aqc_set_y_compensation): what keeping y's low part costs per step."""
+    import torch
+
+    from instances import generate_ec3
+    from paper_1311_3938_gb300 import hamiltonians as HB
+    from paper_1311_3938_gb300.engine import Context
+    import paper_1311_3938_gb300 as P
+
+    n = a.n
+    ctx = Context(n, P.AQC_C64, extra_vector=True)
+    HB.load_ec3(ctx, generate_ec3(n, SEED))
+    ctx.set_schedule(T_RUN, HB.linear_schedule())
+    ctx.set_integrator(0, 0.0)
+    ctx.set_y_compensation(True)
+    ctx.set_initial_state("uniform")
+    ctx.propagate(4, stats=False)
+    ms = []
+    for _ in range(3):
+        st = ctx.propagate(pec, stats=True)
+        ms.append(st["elapsed_ms"] / pec)
+    torch.cuda.synchronize()
+    ctx.close()
+    torch.cuda.empty_cache()
+    step_ms = statistics.median(ms)
+    return {"what": "PEC step with the compensated corrector (y's low part read and written: 9 N b algorithmic)",
+            "pec_step_ms": step_ms,
+            "alg_GBs_9Nb": 9 * (1 << n) * 8 / (step_ms * 1e-3) / 1e9,
+            "alg_GBs_7Nb": 7 * (1 << n) * 8 / (step_ms * 1e-3) / 1e9}
+
+
 def measure_small(a, reps=30):
     """The small-state workload alone: EC3 n = 10 seed 1, linear path, T = 20, uniform start,
     complex128; host wall time per whole solve (initial state, every grid step, P_1 readback),
-    step by step and with CUDA-graph replays of 16 PEC steps."""
+    step by step, with CUDA-graph replays of 16 PEC steps, and with replays of 64 steps on 8-bit
+    tiles (the one-tile step runs on one SM at the FP64 rate; 8-bit tiles spread it over 4)."""
     import statistics as S
 
     from instances import generate_ec3
@@ -522,9 +556,11 @@ def measure_small(a, reps=30):
 
     inst = generate_ec3(10, 1)
     out = {"workload": "ec3-n10-seed1-linear-T20-uniform, complex128, one context"}
-    for label, k in (("step_by_step", 0), ("graph_replay", 16)):
+    for label, k, tb in (("step_by_step", 0, 0), ("graph_replay", 16, 0), ("graph_replay_8bit_tiles", 64, 8)):
         ctx = Context(10, P.AQC_C128)
         ctx.set_graph_steps(k)
+        if tb:
+            ctx.set_tile_bits(tb)
         HB.load_ec3(ctx, inst)
         ctx.set_schedule(20.0, HB.linear_schedule())
         ctx.set_integrator(0, 0.0)
@@ -543,10 +579,11 @@ def measure_small(a, reps=30):
                       "grid_steps_per_s": steps / S.median(walls), "kernels_per_solve": ctx.launch_count() - l0,
                       "graph_replays": ctx.graph_replays(), "P1": P1}
         out["grid_steps"] = steps
-        if k:
+        if k and not tb:
             out["_state"] = ctx.state()
         ctx.close()
-    out["speedup"] = out["step_by_step"]["wall_ms_p50"] / out["graph_replay"]["wall_ms_p50"]
+    out["speedup"] = out["step_by_step"]["wall_ms_p50"] / min(out["graph_replay"]["wall_ms_p50"],
+                                                            out["graph_replay_8bit_tiles"]["wall_ms_p50"])
     return out
 
 
@@ -747,6 +784,7 @@ def run_ours(a):
                 if j.n <= ORACLE_MAX_N:
                     checks.submit(("serve", j.jid), OracleChecks.spec_of(j))
     xy = None if (a.no_xy or not solo) else measure_xy(a)
+    ycomp = None if (a.no_ycomp or not solo) else measure_ycomp(a)
     batched = None if (a.no_batch or not solo) else measure_batched(a, checks)
     serving = None if (a.no_serve or not solo) else measure_serving(a)
     if checks is not None:
@@ -837,6 +875,7 @@ def run_ours(a):
         "batched": batched,
         "serving": serving,
         "oracle_checks": oracle_note,
+        "y_compensation": ycomp,
         "xy_algorithm": xy,
     }
     if r128 is not None:

@@ -239,6 +239,19 @@ int aqc_set_slab_bits(aqc_ctx *ctx, int slab_bits);
  * other k_steps; a failed capture returns AQC_E_CUDA from aqc_propagate. */
 int aqc_set_graph_steps(aqc_ctx *ctx, int k_steps);
 
+/* Turn of layouts for the PEC steps of Sec. I.B (this library's pass order): the fused step
+ * kernel alternates between tile layouts 0 and 1 and, besides completing f_{n+1} = -i H p_{n+1},
+ * the corrector and the predictor p_{n+2}, applies its own layout's products at the next step's
+ * weights to p_{n+2} (restaged from L2 right after it is written), leaving that partial sum for
+ * the next step, which then skips one partial pass: (3k + 4) N b per step instead of
+ * (3k + 5) N b for k >= 2 layouts.  Applies on the fixed-step grid with per-CTA tiles, outside
+ * batches, the slab order and clause-by-clause sequences, and when the products no layout holds
+ * can stay in a partial pass (k >= 3, or none of them).  mode: 0 off (the default: on GB300 the
+ * turned step measured slower, 4.71 against 4.37 ms at 28 qubits in complex64), 1 or -1 on where
+ * it applies.  Results equal those of the plain pass order up to the order in which the
+ * layouts' sums are added.  AQC_E_INVAL for other modes. */
+int aqc_set_layout_turns(aqc_ctx *ctx, int mode);
+
 /* Compensated corrector for complex64 states (reading of the FP32 state, Sec. I.B): each PEC
  * step adds its increment h/24 (9 f_{n+1} + 19 f_n - 5 f_{n-1} + f_{n-2}) to y as an exact
  * two-sum and keeps the rounding in a second complex64 vector (the workspace's extra vector,

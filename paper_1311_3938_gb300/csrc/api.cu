@@ -100,7 +100,7 @@ WsPlan plan_workspace(int n, int prec, unsigned flags = 0) {
   w.off_sync = w.off_counter + 256;  // slab work counter + per-slab counters
   w.off_perm = w.off_sync + align_up((1 + kMaxSlabs) * sizeof(unsigned), 256);  // bit-permutation tables
   w.off_wdev = w.off_perm + 4 * 256 * sizeof(uint32_t);  // weights of graph-replayed steps
-  w.off_partials = w.off_wdev + align_up(3 * kMaxGraphSteps * sizeof(double), 256);
+  w.off_partials = w.off_wdev + align_up((size_t)kGraphStepWeights * kMaxGraphSteps * sizeof(double), 256);
   // k_apply grids are persistent (at most kMaxApplyGrid CTAs); k_norm2 uses reduce_grid()
   size_t g = std::max((size_t)kMaxApplyGrid, (size_t)reduce_grid((uint64_t)1 << n));
   w.partial_doubles = 3 * g;
@@ -199,18 +199,23 @@ struct aqc_ctx {
   // written the K steps' weights to d_wdev
   int graph_req = -1;             // 0 off, -1 automatic, K > 0 (a multiple of 4, <= kMaxGraphSteps)
   int grid_limit = 0;             // > 0: CTAs per layout-pass launch at most (aqc_set_grid_limit)
+  // turn of layouts (aqc_set_layout_turns): the fused step alternates between layouts 0 and 1
+  // and leaves its layout's products of p_{n+2} in q, so the next step skips that pass
+  int turn_req = 0;               // 0 off (default), 1 or -1: on where it applies
+  int q_ready = -1;               // layout whose products of the current p are already in q, or -1
   double* d_wdev = nullptr;       // 3 K weights of the replayed steps
   const double* cur_wdev = nullptr;  // set while a capture is issuing step j: d_wdev + 3 j
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   struct GraphKey {
-    int K = 0, phase = 0;
+    int K = 0, phase = 0, q_ready = -1;
     double h = 0.0;
     int64_t tables = -1;
     uint32_t n_slabs = 0;
     void* vec[V_COUNT] = {};
   } gkey;
   int64_t g_launches = 0;         // kernel launches in one replay
+  int g_q_ready_end = -1;         // q_ready after one replay
   int64_t graph_replays = 0;
   int64_t tables_version = 0;     // bumped by every table build
 
@@ -421,6 +426,7 @@ void plan_slabs(aqc_ctx* c) {
 
 int build_tables(aqc_ctx* c) {
   c->tables_version++;
+  c->q_ready = -1;
   plan_layouts(c);
   DevTables* t = c->h_tab;
   memset(t, 0, sizeof(DevTables));
@@ -766,6 +772,7 @@ ApplyParams base_params(aqc_ctx* c) {
 // With top >= 0, only the partial passes of layouts top .. 1 run (the first of them adds the
 // products no layout holds); the caller finishes the evaluation.
 int evaluate(aqc_ctx* c, const double w[3], const void* src, ApplyParams fin, void* partial_out, int top = -1) {
+  c->q_ready = -1;  // the passes below overwrite q
   const int nl = (int)c->layouts.size();
   const int hi = top >= 0 ? top : nl - 1, lo = top >= 0 ? 1 : 0;
   for (int l = hi; l >= lo; l--) {
@@ -903,6 +910,93 @@ int pec_step_slabs(aqc_ctx* c, const double w[3], const ApplyParams& fin) {
   return AQC_OK;
 }
 
+// The turn of layouts applies where every pass is a per-CTA tile pass of a fixed-step grid and
+// the products no layout holds (gathered from all of p) can stay in a partial pass.
+bool turn_applies(const aqc_ctx* c) {
+  const int nl = (int)c->layouts.size();
+  if (c->turn_req == 0 || c->adaptive || c->in_batch || c->slab.n_slabs || c->step_class >= 0 || nl < 2) return false;
+  for (const Layout& L : c->layouts)
+    if (L.cb > 0) return false;
+  return nl >= 3 || c->n_remote == 0;
+}
+
+// One PEC step with the turn of layouts (Sec. I.B step; the layout order is this library's):
+// q holds layout Xp's products of p_{n+1} (Xp = q_ready, or -1); the layouts other than Xp and
+// the fused layout Xc add theirs as partial passes (the first one also the products no layout
+// holds); the fused step on Xc completes f_{n+1}, corrects y, predicts p_{n+2} and leaves Xc's
+// products of p_{n+2} at the next weights in q.  Xc alternates between layouts 0 and 1.
+int pec_step_turn(aqc_ctx* c, const ApplyParams& fin0, const double w[3]) {
+  const int nl = (int)c->layouts.size();
+  const int Xp = c->q_ready, Xc = Xp == 0 ? 1 : 0;
+  double w2[3];
+  sched_weights(c, c->seg_t0 + (double)(c->step + 2) * c->h, w2);
+  bool any = false;
+  for (int l = nl - 1; l >= 0; l--) {
+    if (l == Xp || l == Xc) continue;
+    const bool first = !any;
+    ApplyParams p = base_params(c);
+    p.mode = MODE_PARTIAL;
+    p.L = c->layouts[l];
+    p.layout_index = l;
+    p.with_diag = 0;
+    p.with_remote = first;
+    for (int g = 0; g < 3; g++) p.w[g] = w[g];
+    p.wdev = c->cur_wdev;
+    p.src = c->vec[V_P];
+    p.qin = (first && Xp < 0) ? nullptr : c->vec[V_Q];
+    p.qout = c->vec[V_Q];
+    p.ntiles = 1u << (c->n - p.L.t);
+    any = true;
+    if (c->xpartial[l] && !(first && c->n_remote > 0)) {
+      XPartialParams x;
+      memset(&x, 0, sizeof(x));
+      x.tma_rank = encode_tile_map(&x.tmap, p.src, c->n, p.L);
+      if (x.tma_rank) {
+        x.tab = c->d_tab;
+        x.L = p.L;
+        x.layout_index = l;
+        for (int g = 0; g < 3; g++) x.w[g] = w[g];
+        x.wdev = c->cur_wdev;
+        x.max_grid = c->grid_limit;
+        x.qin = p.qin;
+        x.qout = p.qout;
+        x.ntiles = p.ntiles;
+        x.slots = c->d_slots;
+        CUDA_TRY(c, launch_partial_x(x, (int)xpartial_smem_bytes(c->nplain[l] + c->nhop[l]), c->stream));
+        c->launches++;
+        continue;
+      }
+    }
+    const size_t smem = apply_smem_bytes(c->prec, p.L.t, c->nplain[l], c->ngeneral[l] + (first ? c->n_remote : 0), 0);
+    if (smem > 227 * 1024) FAIL(c, AQC_E_UNSUPPORTED, "shared memory %zu bytes too large", smem);
+    CUDA_TRY(c, launch_apply(c->prec, p, (int)smem, c->stream));
+    c->launches++;
+  }
+  ApplyParams f = fin0;
+  f.L = c->layouts[Xc];
+  f.layout_index = Xc;
+  f.with_diag = 1;
+  f.with_remote = !any;  // only when no partial pass ran, i.e. with no products no layout holds
+  for (int g = 0; g < 3; g++) {
+    f.w[g] = w[g];
+    f.w2[g] = w2[g];
+  }
+  f.wdev = c->cur_wdev;
+  f.turn = 1;
+  f.src = c->vec[V_P];
+  f.qin = (!any && Xp < 0) ? nullptr : c->vec[V_Q];
+  f.qout = c->vec[V_Q];
+  f.dcode = c->table_class >= 0 ? c->d_dcode : nullptr;
+  f.ntiles = 1u << (c->n - f.L.t);
+  const size_t smem = apply_smem_bytes(c->prec, f.L.t, c->nplain[Xc], c->ngeneral[Xc] + (any ? 0 : c->n_remote), c->n_z) +
+                      table_smem_bytes(c->prec, f.L.t, c->nplain[Xc], c->ngeneral[Xc], 0);
+  if (smem > 227 * 1024) FAIL(c, AQC_E_UNSUPPORTED, "shared memory %zu bytes too large", smem);
+  CUDA_TRY(c, launch_apply(c->prec, f, (int)smem, c->stream));
+  c->launches++;
+  c->q_ready = Xc;
+  return AQC_OK;
+}
+
 int pec_step(aqc_ctx* c) {
   const int64_t n = c->step;
   double w[3];
@@ -919,7 +1013,11 @@ int pec_step(aqc_ctx* c) {
   // under step-size control y_{n+1} goes to the scratch vector, so a rejected step keeps y_n
   fin.yout = c->adaptive ? c->vec[V_ACC] : nullptr;
   fin.ylo = c->ycomp ? c->vec_save : nullptr;
-  int rc = (c->slab.n_slabs && !c->ycomp) ? pec_step_slabs(c, w, fin) : evaluate(c, w, c->vec[V_P], fin, nullptr);
+  int rc;
+  if (turn_applies(c))
+    rc = pec_step_turn(c, fin, w);
+  else
+    rc = (c->slab.n_slabs && !c->ycomp) ? pec_step_slabs(c, w, fin) : evaluate(c, w, c->vec[V_P], fin, nullptr);
   if (rc) return rc;
   c->evals++;
   return AQC_OK;  // the caller counts the step (count_step) or decides on it (control_step)
@@ -941,6 +1039,7 @@ int begin_segment(aqc_ctx* c, double t0, double hp, int64_t m_given = 0) {
   c->seg_t0 = t0;
   c->step = 0;
   c->hist_ready = false;
+  c->q_ready = -1;
   c->small_run = 0;
   c->seg_done0 = c->steps_done;
   if (c->adaptive)  // kept until the segment's first PEC step is accepted
@@ -1026,6 +1125,7 @@ aqc_ctx::GraphKey graph_key(const aqc_ctx* c, int K) {
   aqc_ctx::GraphKey k;
   k.K = K;
   k.phase = (int)(c->step & 3);
+  k.q_ready = c->q_ready;
   k.h = c->h;
   k.tables = c->tables_version;
   k.n_slabs = c->slab.n_slabs;
@@ -1034,7 +1134,8 @@ aqc_ctx::GraphKey graph_key(const aqc_ctx* c, int K) {
 }
 
 bool same_key(const aqc_ctx::GraphKey& a, const aqc_ctx::GraphKey& b) {
-  if (a.K != b.K || a.phase != b.phase || memcmp(&a.h, &b.h, sizeof(double)) != 0 || a.tables != b.tables ||
+  if (a.K != b.K || a.phase != b.phase || a.q_ready != b.q_ready || memcmp(&a.h, &b.h, sizeof(double)) != 0 ||
+      a.tables != b.tables ||
       a.n_slabs != b.n_slabs)
     return false;
   for (int v = 0; v < V_COUNT; v++)
@@ -1054,13 +1155,14 @@ int capture_steps(aqc_ctx* c, int K) {
   drop_step_graph(c);
   if (!c->cap_stream) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   const int64_t step0 = c->step, evals0 = c->evals, launches0 = c->launches;
+  const int q_ready0 = c->q_ready;
   cudaStream_t user = c->stream;
   c->stream = c->cap_stream;
   cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
   int rc = AQC_OK;
   if (e == cudaSuccess) {
     for (int j = 0; j < K && rc == AQC_OK; j++) {
-      c->cur_wdev = c->d_wdev + 3 * j;
+      c->cur_wdev = c->d_wdev + kGraphStepWeights * j;
       rc = pec_step(c);
       c->step++;
     }
@@ -1070,9 +1172,11 @@ int capture_steps(aqc_ctx* c, int K) {
   const cudaError_t e_end = e == cudaSuccess ? cudaStreamEndCapture(c->cap_stream, &graph) : e;
   c->stream = user;
   c->g_launches = c->launches - launches0;
+  c->g_q_ready_end = c->q_ready;
   c->step = step0;
   c->evals = evals0;
   c->launches = launches0;
+  c->q_ready = q_ready0;
   if (rc != AQC_OK) {
     if (graph) cudaGraphDestroy(graph);
     return rc;
@@ -1087,7 +1191,7 @@ int capture_steps(aqc_ctx* c, int K) {
     c->gexec = nullptr;
     FAIL(c, AQC_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
   }
-  c->gkey = graph_key(c, K);
+  c->gkey = graph_key(c, K);  // the key of the state the replays start from
   return AQC_OK;
 }
 
@@ -1098,13 +1202,17 @@ int pec_steps_graph(aqc_ctx* c, int K) {
     int rc = capture_steps(c, K);
     if (rc) return rc;
   }
-  double wb[3 * kMaxGraphSteps];
-  for (int j = 0; j < K; j++) sched_weights(c, c->seg_t0 + (double)(c->step + j + 1) * c->h, wb + 3 * j);
-  CUDA_TRY(c, launch_set_weights(c->d_wdev, wb, 3 * K, c->stream));
+  double wb[kGraphStepWeights * kMaxGraphSteps];
+  for (int j = 0; j < K; j++) {
+    sched_weights(c, c->seg_t0 + (double)(c->step + j + 2) * c->h, wb + kGraphStepWeights * j + 3);
+    sched_weights(c, c->seg_t0 + (double)(c->step + j + 1) * c->h, wb + kGraphStepWeights * j);
+  }
+  CUDA_TRY(c, launch_set_weights(c->d_wdev, wb, kGraphStepWeights * K, c->stream));
   CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->stream));
   c->launches += 1 + c->g_launches;
   c->evals += K;
   c->graph_replays++;
+  c->q_ready = c->g_q_ready_end;
   for (int j = 0; j < K; j++) count_step(c);
   return AQC_OK;
 }
@@ -1545,6 +1653,16 @@ int aqc_set_y_compensation(aqc_ctx* ctx, int enable) {
   return AQC_OK;
 }
 
+int aqc_set_layout_turns(aqc_ctx* ctx, int mode) {
+  if (!ctx) return AQC_E_INVAL;
+  if (mode < -1 || mode > 1) FAIL(ctx, AQC_E_INVAL, "mode must be -1, 0 or 1");
+  ctx->turn_req = mode;
+  ctx->q_ready = -1;
+  DeviceGuard dg(ctx->device);
+  drop_step_graph(ctx);
+  return AQC_OK;
+}
+
 int aqc_set_grid_limit(aqc_ctx* ctx, int max_ctas) {
   if (!ctx) return AQC_E_INVAL;
   if (max_ctas < 0) FAIL(ctx, AQC_E_INVAL, "max_ctas must be >= 0");
@@ -1670,6 +1788,7 @@ int aqc_set_initial_state(aqc_ctx* ctx, int kind, uint64_t basis, const void* us
   ctx->evals = 0;
   ctx->nsteps = 0;
   ctx->hist_ready = false;
+  ctx->q_ready = -1;
   ctx->steps_done = 0;
   ctx->at_end = false;
   ctx->rejects = 0;

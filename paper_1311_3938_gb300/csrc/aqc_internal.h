@@ -119,6 +119,9 @@ struct ApplyParams {
   const double* wdev; // nullable: read the weights from this device array instead of w (steps
                       // replayed from a CUDA graph, whose weights the host writes before a replay)
   int max_grid;       // > 0: at most this many CTAs (the kernels are persistent over tiles)
+  int turn;           // STEP: also apply this layout's products, at the weights w2 (wdev[3..5]
+                      // when wdev is set), to the new predictor p_{n+2}; the sum goes to qout
+  double w2[3];
   double h;
   const uint8_t* dcode; // per-index clause counts of class table_class (nullable)
   const void* src;   // vector the Hamiltonian acts on
@@ -241,8 +244,10 @@ constexpr int kSlotFault = 5;  // nonzero: an inter-CTA wait gave up (results of
 constexpr int kSlotCount = 8;
 
 // PEC steps per CUDA-graph replay of a lone context: at most this many; the weights of each
-// replayed step come from a device array of 3 doubles per step (ApplyParams::wdev)
+// replayed step come from a device array of kGraphStepWeights doubles per step
+// (ApplyParams::wdev: the weights at t_{n+1}, then at t_{n+2} for the turn of layouts)
 constexpr int kMaxGraphSteps = 64;
+constexpr int kGraphStepWeights = 6;
 
 cudaError_t launch_apply(int prec, const ApplyParams& p, int smem_bytes, cudaStream_t s);
 int apply_grid(int prec, int mode, uint32_t ntiles, int smem_bytes);
@@ -266,8 +271,8 @@ cudaError_t launch_predict(int prec, void* p, const void* y, const void* f3, con
 cudaError_t launch_reduce(int prec, int what, const void* a, uint64_t N, double* partials, unsigned* counter,
                           double* slots, int grid, cudaStream_t s);
 cudaError_t launch_fidelity(int prec, const void* a, uint64_t w, double* slots, cudaStream_t s);
-// dst[0 .. count) = w[0 .. count), count <= 3 kMaxGraphSteps, the values passed as kernel
-// arguments (no host buffer outlives the call)
+// dst[0 .. count) = w[0 .. count), count <= kGraphStepWeights kMaxGraphSteps, the values passed
+// as kernel arguments (no host buffer outlives the call)
 cudaError_t launch_set_weights(double* dst, const double* w, int count, cudaStream_t s);
 // k_fma64: `blocks` CTAs of 256 threads, each thread `iters` rounds of independent FP64 FMAs;
 // fma64_count gives the FMAs one launch performs

@@ -963,7 +963,7 @@ __device__ __forceinline__ void process_tile(const TileCtx<R>& T, uint32_t zb, u
   }
 }
 
-template <typename R, int MODE, bool CL, bool COMP = false>
+template <typename R, int MODE, bool CL, bool COMP = false, bool TURN = false>
 __global__ void __launch_bounds__(kThreads, (MODE == MODE_PARTIAL && sizeof(R) == 4 && !CL) ? 3 : 2)
     k_apply(const ApplyParams P) {
   using C2 = typename Cplx<R>::T;
@@ -989,6 +989,25 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_PARTIAL && sizeof(R) =
   T.pout = reinterpret_cast<C2*>(P.pout);
   T.acc = reinterpret_cast<C2*>(P.acc);
   T.ylo = reinterpret_cast<C2*>(P.ylo);
+  // TURN: the same layout's products (no diagonal, no remote products) at the next weights,
+  // applied to the new predictor once a tile's step is done; tables after T's
+  TileCtx<R> T2;
+  if (TURN) {
+    const SmemMap<R> mapA(T.tsize, T.np, T.ng, T.nz);
+    const double v0 = P.wdev ? P.wdev[3] : P.w2[0], v1 = P.wdev ? P.wdev[4] : P.w2[1],
+                 v2 = P.wdev ? P.wdev[5] : P.w2[2];
+    load_coefficients<R>(T2, P.tab, P.L, P.layout_index, false, false, nullptr, v0, v1, v2, smem, smem + mapA.total);
+    T2.stage = 0;
+    T2.h = (R)P.h;
+    set_h24(T2, P.h);
+    T2.step_k = 0;
+    T2.step_wdone = T2.step_wact = (R)0;
+    T2.src = reinterpret_cast<const C2*>(P.pout);
+    T2.qin = nullptr;
+    T2.qout = reinterpret_cast<C2*>(P.qout);
+    T2.y = T2.yout = T2.fout = T2.pout = T2.acc = T2.ylo = nullptr;
+    T2.f0 = T2.f1 = T2.f2 = nullptr;
+  }
 
   // reductions: per-thread partials over one tile in the state precision (a few dozen
   // points), promoted to FP64 once per tile; FP64 across tiles, CTAs and the grid
@@ -1007,6 +1026,10 @@ __global__ void __launch_bounds__(kThreads, (MODE == MODE_PARTIAL && sizeof(R) =
     process_tile<R, MODE, CL, 0, true, COMP>(T, tile_base(T.L, tile), rank, rt0, rt1);
     red[0] += (double)rt0;
     red[1] += (double)rt1;
+    if (TURN) {  // the tile's p_{n+2} was just stored by this CTA: restaged from L2
+      R u0 = (R)0, u1 = (R)0;
+      process_tile<R, MODE_PARTIAL, false>(T2, tile_base(T.L, tile), 0u, u0, u1);
+    }
   }
   if (CL) cg::this_cluster().sync();  // no CTA leaves while others may read its shared memory
 
@@ -1236,10 +1259,10 @@ size_t apply_smem_bytes(int prec, int t, int n_plain, int n_general, int n_z) {
 
 // Persistent grid: (resident CTAs per SM for this smem size) x SMs, at most one CTA per tile;
 // for cluster layouts, the number of clusters that can be resident at once (x cluster size).
-template <typename R, int MODE, bool CL, bool COMP>
+template <typename R, int MODE, bool CL, bool COMP, bool TURN>
 static cudaError_t grid_for(uint32_t ntiles, int smem, cudaStream_t s, int* grid) {
   static int configured = 0, cached_smem = -1, cached_dev = -1, cached_g = 0;
-  auto kern = k_apply<R, MODE, CL, COMP>;
+  auto kern = k_apply<R, MODE, CL, COMP, TURN>;
   if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -1291,10 +1314,10 @@ static cudaError_t grid_for(uint32_t ntiles, int smem, cudaStream_t s, int* grid
   return cudaSuccess;
 }
 
-template <typename R, int MODE, bool CL, bool COMP = false>
+template <typename R, int MODE, bool CL, bool COMP = false, bool TURN = false>
 static cudaError_t launch_one(const ApplyParams& p, int smem, cudaStream_t s) {
   int grid = 0;
-  cudaError_t e = grid_for<R, MODE, CL, COMP>(p.ntiles, smem, s, &grid);
+  cudaError_t e = grid_for<R, MODE, CL, COMP, TURN>(p.ntiles, smem, s, &grid);
   if (e != cudaSuccess) return e;
   if (p.max_grid > 0 && grid > p.max_grid) {  // whole clusters, at least one
     const int unit = CL ? (1 << kClusterBits) : 1;
@@ -1314,10 +1337,10 @@ static cudaError_t launch_one(const ApplyParams& p, int smem, cudaStream_t s) {
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_apply<R, MODE, CL, COMP>, p);
+    e = cudaLaunchKernelEx(&cfg, k_apply<R, MODE, CL, COMP, TURN>, p);
     if (e != cudaSuccess) return e;
   } else {
-    k_apply<R, MODE, CL, COMP><<<grid, kThreads, smem, s>>>(p);
+    k_apply<R, MODE, CL, COMP, TURN><<<grid, kThreads, smem, s>>>(p);
   }
   return cudaGetLastError();
 }
@@ -1327,11 +1350,18 @@ static cudaError_t launch_prec(const ApplyParams& p, int smem, cudaStream_t s) {
   switch (p.mode) {
     case MODE_PARTIAL: return launch_one<R, MODE_PARTIAL, CL>(p, smem, s);
     case MODE_STEP:
-      // the compensated corrector (complex64, per-CTA tiles) is an instantiation of its own
-      if constexpr (sizeof(R) == 4 && !CL) {
-        if (p.ylo) return launch_one<R, MODE_STEP, CL, true>(p, smem, s);
+      // the compensated corrector (complex64) and the turn of layouts (per-CTA tiles) are
+      // instantiations of their own
+      if constexpr (!CL) {
+        if constexpr (sizeof(R) == 4) {
+          if (p.ylo) return p.turn ? launch_one<R, MODE_STEP, CL, true, true>(p, smem, s)
+                                   : launch_one<R, MODE_STEP, CL, true, false>(p, smem, s);
+        } else {
+          if (p.ylo) return cudaErrorInvalidValue;
+        }
+        if (p.turn) return launch_one<R, MODE_STEP, CL, false, true>(p, smem, s);
       } else {
-        if (p.ylo) return cudaErrorInvalidValue;
+        if (p.ylo || p.turn) return cudaErrorInvalidValue;
       }
       return launch_one<R, MODE_STEP, CL>(p, smem, s);
     case MODE_RK4: return launch_one<R, MODE_RK4, CL>(p, smem, s);
@@ -1534,7 +1564,7 @@ cudaError_t launch_fma64(int blocks, int iters, cudaStream_t s) {
 int64_t fma64_count(int blocks, int iters) { return (int64_t)blocks * 256 * kFmaChains * iters; }
 
 struct GraphWeights {
-  double w[3 * kMaxGraphSteps];
+  double w[kGraphStepWeights * kMaxGraphSteps];
 };
 
 __global__ void k_set_weights(double* dst, const GraphWeights W, int count) {
@@ -1543,11 +1573,11 @@ __global__ void k_set_weights(double* dst, const GraphWeights W, int count) {
 }
 
 cudaError_t launch_set_weights(double* dst, const double* w, int count, cudaStream_t s) {
-  if (count < 0 || count > 3 * kMaxGraphSteps) return cudaErrorInvalidValue;
+  if (count < 0 || count > kGraphStepWeights * kMaxGraphSteps) return cudaErrorInvalidValue;
   GraphWeights W;
   for (int i = 0; i < count; i++) W.w[i] = w[i];
-  for (int i = count; i < 3 * kMaxGraphSteps; i++) W.w[i] = 0.0;
-  k_set_weights<<<1, 3 * kMaxGraphSteps, 0, s>>>(dst, W, count);
+  for (int i = count; i < kGraphStepWeights * kMaxGraphSteps; i++) W.w[i] = 0.0;
+  k_set_weights<<<1, kGraphStepWeights * kMaxGraphSteps, 0, s>>>(dst, W, count);
   return cudaGetLastError();
 }
 

@@ -114,6 +114,10 @@ class Context:
         """PEC steps per CUDA-graph replay: 0 off, -1 automatic, or a multiple of 4 up to 64."""
         N.aqc_set_graph_steps(self.handle, k_steps)
 
+    def set_layout_turns(self, mode=1):
+        """Turn of layouts of the PEC step (aqc_set_layout_turns): 0 off (default), 1 on."""
+        N.aqc_set_layout_turns(self.handle, mode)
+
     def set_y_compensation(self, enable=True):
         """Compensated complex64 corrector (aqc_set_y_compensation); set the initial state after."""
         N.aqc_set_y_compensation(self.handle, enable)
