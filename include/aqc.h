@@ -460,6 +460,15 @@ int aqc_norm2_noalloc(int precision, const void *psi, uint64_t n_amplitudes, voi
  * aqc_last_error(NULL).  The paper has no counterpart. */
 int aqc_measure_fp64_fma(int device, void *cuda_stream, int iters, double *tflops_out, double *ms_out);
 
+/* Self-test of the bounded waits (the paper has no counterpart): the library's kernels that wait
+ * on other CTAs or on tensor copies poll a bounded number of times and, on giving up, set a fault
+ * slot that the next aqc_propagate with stats reports as AQC_E_TIMEOUT.  This call runs that
+ * give-up path on purpose, without any fault: one thread waits for a workspace flag that nothing
+ * sets, for `polls` polls of about 1 us, records the give-up, and the host returns AQC_E_TIMEOUT
+ * and clears the slot, so the context stays usable.  polls in [1, 10^7] (else AQC_E_INVAL).
+ * Synchronises the context stream. */
+int aqc_wait_selftest(aqc_ctx *ctx, int64_t polls);
+
 /* Total kernel launches the context has issued since creation (monotone counter). */
 int aqc_launch_count(const aqc_ctx *ctx, int64_t *out);
 

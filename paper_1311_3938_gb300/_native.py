@@ -117,6 +117,7 @@ def lib():
             "aqc_set_grid_limit": (i32, [vp, i32]),
             "aqc_set_y_compensation": (i32, [vp, i32]),
             "aqc_set_layout_turns": (i32, [vp, i32]),
+            "aqc_wait_selftest": (i32, [vp, i64]),
             "aqc_measure_fp64_fma": (i32, [i32, vp, i32, C.POINTER(dbl), C.POINTER(dbl)]),
             "aqc_get_graph_replays": (i32, [vp, C.POINTER(i64)]),
             "aqc_batch_workspace_bytes": (sz, [i32, i64]),
@@ -333,6 +334,10 @@ def aqc_tridiag_eigvec(a, b, lam):
 
 def aqc_set_graph_steps(ctx, k_steps):
     _check(ctx, lib().aqc_set_graph_steps(ctx, int(k_steps)))
+
+
+def aqc_wait_selftest(ctx, polls):
+    _check(ctx, lib().aqc_wait_selftest(ctx, int(polls)))
 
 
 def aqc_set_layout_turns(ctx, mode):

@@ -1653,6 +1653,29 @@ int aqc_set_y_compensation(aqc_ctx* ctx, int enable) {
   return AQC_OK;
 }
 
+int aqc_wait_selftest(aqc_ctx* ctx, int64_t polls) {
+  if (!ctx) return AQC_E_INVAL;
+  if (polls < 1 || polls > 10000000) FAIL(ctx, AQC_E_INVAL, "polls must be in [1, 10^7]");
+  DeviceGuard dg(ctx->device);
+  unsigned* flag = reinterpret_cast<unsigned*>(ctx->d_slots + kSlotWaitFlag);
+  CUDA_TRY(ctx, cudaMemsetAsync(flag, 0, sizeof(double), ctx->stream));
+  CUDA_TRY(ctx, launch_wait_flag(flag, polls, ctx->d_slots, ctx->stream));
+  ctx->launches++;
+  double fault = 0.0;
+  CUDA_TRY(ctx, cudaMemcpyAsync(&fault, ctx->d_slots + kSlotFault, sizeof(double), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (fault != 0.0) {
+    const double zero = 0.0;
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_slots + kSlotFault, &zero, sizeof(double), cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    FAIL(ctx, AQC_E_TIMEOUT, "the wait gave up after %lld polls (self-test: nothing sets its flag)",
+         (long long)polls);
+  }
+  return AQC_OK;
+}
+
 int aqc_set_layout_turns(aqc_ctx* ctx, int mode) {
   if (!ctx) return AQC_E_INVAL;
   if (mode < -1 || mode > 1) FAIL(ctx, AQC_E_INVAL, "mode must be -1, 0 or 1");

@@ -277,6 +277,10 @@ cudaError_t launch_set_weights(double* dst, const double* w, int count, cudaStre
 // k_fma64: `blocks` CTAs of 256 threads, each thread `iters` rounds of independent FP64 FMAs;
 // fma64_count gives the FMAs one launch performs
 cudaError_t launch_fma64(int blocks, int iters, cudaStream_t s);
+// k_wait_flag: one thread waits for *flag != 0 for at most `polls` polls (~1 us each); giving
+// up sets slots[kSlotFault]
+cudaError_t launch_wait_flag(const unsigned* flag, int64_t polls, double* slots, cudaStream_t s);
+constexpr int kSlotWaitFlag = 6;  // a slot whose bits serve as the self-test's flag (never set)
 int64_t fma64_count(int blocks, int iters);
 int reduce_grid(uint64_t N);
 cudaError_t launch_batch(int prec, int threads, const BatchLaunch& b, int nitems, int smem, cudaStream_t s);

@@ -1536,6 +1536,25 @@ cudaError_t launch_predict(int prec, void* p, const void* y, const void* f3, con
   return cudaGetLastError();
 }
 
+// ---- bounded wait (the give-up path of the library's inter-CTA and copy waits) -------------
+// One thread polls `flag` (acquire loads, ~1 us apart) until it is nonzero or `polls` polls have
+// passed; giving up sets slots[kSlotFault], as the TMA and slab waits do.
+__global__ void k_wait_flag(const unsigned* flag, int64_t polls, double* slots) {
+  if (threadIdx.x != 0) return;
+  for (int64_t i = 0; i < polls; i++) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(flag) : "memory");
+    if (v != 0u) return;
+    __nanosleep(1000);
+  }
+  slots[kSlotFault] = 1.0;
+}
+
+cudaError_t launch_wait_flag(const unsigned* flag, int64_t polls, double* slots, cudaStream_t s) {
+  k_wait_flag<<<1, 32, 0, s>>>(flag, polls, slots);
+  return cudaGetLastError();
+}
+
 // ---- FP64 FMA throughput (the denominator of the complex128 step's ALU roofline) -------
 __device__ double g_fma_sink;
 
