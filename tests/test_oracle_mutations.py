@@ -3,6 +3,9 @@ term, a wrong coefficient, a wrong stage time, a transposed index — is written
 copy of the C oracle, and at least one pin of tests/test_oracle_pins.py must fail with it.
 The clause-by-clause coefficients of Eq. kpath get three: the two segment weights swapped, the
 partial sum H_k missing its own clause, and the two segments meeting at s = k/m both counted.
+Four more go into the step-size control (the acceptance test, the halving, the restart of a
+rejected start-up, the PEC evaluation time) and three into the XY start (the highest eigenvector,
+the neighbouring sector, the first excited energy), each caught by its own pins.
 This shows the pins are sharp enough to catch mistakes anywhere in the oracle."""
 import ctypes as C
 import os
@@ -56,8 +59,8 @@ PINS = [
 ]
 
 
-def _mutant(tmp_path, name):
-    old, new = MUTATIONS[name]
+def _mutant(tmp_path, name, table=None):
+    old, new = (table or MUTATIONS)[name]
     src = open(SRC).read()
     assert src.count(old) >= 1, name
     mut = src.replace(old, new, 1)
@@ -81,6 +84,10 @@ def _bind(path):
     lib.or_hpsi_at.restype = C.c_int
     lib.or_weights.argtypes = [C.POINTER(O._Sched), C.c_double, C.POINTER(C.c_double)]
     lib.or_weights.restype = None
+    lib.or_propagate_adaptive.argtypes = [C.POINTER(O._Ham), C.POINTER(O._Sched), C.c_double, C.c_double, C.c_int,
+                                          C.c_double, C.c_int64, C.c_void_p, C.POINTER(O._AStats),
+                                          C.POINTER(O._Segment), C.c_int64, C.c_void_p, C.c_int64, C.c_int]
+    lib.or_propagate_adaptive.restype = C.c_int
     return lib
 
 
@@ -149,5 +156,86 @@ def test_planted_mistake_in_xy_builders_is_caught(monkeypatch, name):
         try:
             p()
         except (AssertionError, RuntimeError, ValueError):
+            failed.append(i)
+    assert failed, f"no pin caught the planted mistake {name}"
+
+
+# Planted mistakes in the step-size control (or_propagate_adaptive, reading of Sec. I.B): the
+# acceptance test, the halving, the restart of a segment whose first PEC step is rejected, and
+# the time of the PEC evaluation; each must be caught by a pin of test_oracle_adaptive_pins.py.
+ADAPTIVE_MUTATIONS = {
+    "adaptive_accepts_twice_the_tolerance": ("if (!(est <= lim)) {", "if (!(est <= 2.0 * lim)) {"),
+    "adaptive_quarters_instead_of_halving": ("hp = 0.5 * h;", "hp = 0.25 * h;"),
+    "adaptive_keeps_the_rejected_start_up": ("memcpy(psi, yseg, bytes);", ";"),
+    "adaptive_pec_evaluation_time": ("if (deriv(H, sc, t0 + (double)(kk + 1) * h, p, fnew, tmp, N, nthreads))",
+                                     "if (deriv(H, sc, t0 + (double)kk * h, p, fnew, tmp, N, nthreads))"),
+}
+
+
+def _adaptive_pins():
+    import test_oracle_adaptive_pins as ad
+
+    return [
+        lambda: ad.test_no_rejection_is_the_fixed_grid_bit_for_bit(1),
+        ad.test_unstable_start_is_rejected_down_to_a_stable_step,
+        ad.test_every_accepted_estimate_is_within_tolerance,
+    ]
+
+
+def test_unmutated_step_control_passes_its_pins():
+    O._load()
+    for p in _adaptive_pins():
+        p()
+
+
+@pytest.mark.parametrize("name", sorted(ADAPTIVE_MUTATIONS))
+def test_planted_mistake_in_step_control_is_caught(tmp_path, monkeypatch, name):
+    lib = _bind(_mutant(tmp_path, name, ADAPTIVE_MUTATIONS))
+    monkeypatch.setattr(O, "_lib", lib)
+    failed = []
+    for i, p in enumerate(_adaptive_pins()):
+        try:
+            p()
+        except (AssertionError, RuntimeError):
+            failed.append(i)
+    assert failed, f"no pin caught the planted mistake {name}"
+
+
+# Planted mistakes in the XY start (xy_sector_ground_state): the highest instead of the lowest
+# eigenvector, and a neighbouring Hamming-weight sector.
+GROUND_MUTATIONS = {
+    "xy_ground_highest_eigenvector": ("v = V[:, 0]", "v = V[:, -1]"),
+    "xy_ground_wrong_sector": ('if bin(z).count("1") == k], dtype=np.int64)',
+                               'if bin(z).count("1") == k + 1], dtype=np.int64)'),
+    "xy_ground_energy_of_the_first_excited_level": ("return float(lam[0]), psi", "return float(lam[1]), psi"),
+}
+
+
+def _ground_pins():
+    import test_oracle_xy_pins as xy
+
+    return [
+        lambda: xy.test_xy_ground_state_against_the_hopping_block(8, 1),
+        lambda: xy.test_xy_ground_state_on_the_complete_graph_is_dicke(5),
+        xy.test_xy_ground_state_against_the_kronecker_matrix,
+    ]
+
+
+@pytest.mark.parametrize("name", sorted(GROUND_MUTATIONS))
+def test_planted_mistake_in_the_xy_start_is_caught(monkeypatch, name):
+    import inspect
+    import textwrap
+
+    old, new = GROUND_MUTATIONS[name]
+    src = textwrap.dedent(inspect.getsource(O.xy_sector_ground_state))
+    assert src.count(old) == 1, name
+    ns = dict(vars(O))
+    exec(compile(src.replace(old, new), O.__file__, "exec"), ns)
+    monkeypatch.setattr(O, "xy_sector_ground_state", ns["xy_sector_ground_state"])
+    failed = []
+    for i, p in enumerate(_ground_pins()):
+        try:
+            p()
+        except (AssertionError, RuntimeError, ValueError, IndexError):
             failed.append(i)
     assert failed, f"no pin caught the planted mistake {name}"
