@@ -366,7 +366,9 @@ void aqc_batch_destroy(aqc_batch *b);
 int aqc_batch_set_shape(aqc_batch *b, int threads, int steps_per_round);
 
 /* Add a context that has a Hamiltonian, a schedule and an initial state; its RK4 start-up
- * runs now on the batch stream.  *slot_out receives its slot. */
+ * runs now on the batch stream.  *slot_out receives its slot.  Members run the fixed-step grid
+ * with the plain corrector: a context under step-size control or y compensation, or with a
+ * clause-by-clause sequence, is refused (AQC_E_UNSUPPORTED); a full batch gives AQC_E_NOMEM. */
 int aqc_batch_add(aqc_batch *b, aqc_ctx *ctx, int *slot_out);
 
 /* Remove the member in `slot` and hand its context back. */
