@@ -62,6 +62,51 @@ def test_served_results_equal_alone_and_oracle():
             assert rel_err(served.state, _oracle_state(served)) < TOL_STATE[C64]
 
 
+def test_shortest_first_policy_with_a_capped_large_job():
+    """policy "shortest", one large job at a time with its launches capped at a few CTAs
+    (aqc_set_grid_limit): every request completes, large jobs never overlap, each result equals
+    the job solved alone (a large job's state bit for bit: the cap only lengthens its launches),
+    and a time limit censors what is still running; the one-at-a-time baseline of the same stream
+    gives the same results."""
+    import copy
+
+    from paper_1311_3938_gb300 import workloads as W
+
+    jobs = W.random_jobs(14, 700, n_range=(8, 14), T_range=(0.3, 1.5), rate=100.0, big_every=5, big_n=18,
+                         path_mix=True)
+    srv = W.Server(C64, batch_max_n=14, max_members=16, steps_per_round=8, big_chunk=16, keep_state=True,
+                   policy="shortest", max_large=1, large_grid=8)
+    try:
+        res = srv.serve(copy.deepcopy(jobs))
+    finally:
+        srv.close()
+    assert res["completed"] == len(jobs) and not res["censored_jobs"]
+    big = sorted((j for j in res["jobs"] if j.route == "stream"), key=lambda j: j.admitted)
+    assert len(big) == 2
+    assert big[0].finished <= big[1].admitted  # one large job at a time
+    for served in res["jobs"]:
+        alone = W.solve_single(copy.deepcopy(jobs[served.jid]), keep_state=True)
+        assert served.steps == alone.steps
+        if served.route == "stream":
+            assert np.array_equal(served.state, alone.state)
+        else:
+            assert rel_err(served.state, alone.state) < 2e-6
+    seq = copy.deepcopy(jobs)
+    done, cens, wall = W.serve_one_at_a_time(seq, order="shortest")
+    assert len(done) == len(jobs) and not cens
+    by_id = {j.jid: j for j in res["jobs"]}
+    for j in done:
+        assert j.steps == by_id[j.jid].steps and abs(j.P1 - by_id[j.jid].P1) < 1e-6
+    # a time limit ends the served run with work in flight, released and reported as censored
+    srv = W.Server(C64, batch_max_n=14, max_members=16, steps_per_round=8, big_chunk=16, policy="shortest",
+                   max_large=1, large_grid=8)
+    try:
+        res = srv.serve(copy.deepcopy(jobs), time_limit=0.05)
+    finally:
+        srv.close()
+    assert res["completed"] + len(res["censored_jobs"]) + len(res["not_admitted"]) == len(jobs)
+
+
 def test_admission_respects_hbm_budget():
     import copy
 
